@@ -1,0 +1,70 @@
+"""Block preconditioners B_D and B_T of the SG matrix (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Sec. 4.1: B_D = G_0 (x) K_0 (mean-based, block diagonal); each diagonal
+block is inverted approximately by a multigrid V-cycle.
+Sec. 4.2: B_T = the lower block-triangular part of A, i.e. one block
+Gauss-Seidel step from a zero initial guess; its diagonal blocks are solved
+inexactly by the standard V-cycle.
+
+Reading taken (the paper states B_T for the 2x2 split of Eq.
+(hierarchical_structure) and calls it the lower block-triangular part of A):
+B_T is the full lower block-triangular part of A in the degree-graded PC
+order, which is the 2x2 split applied recursively down to degree 0.  Its
+inverse is applied by plain block forward substitution over the PC index:
+  T_i = R_i - sum_{j<i} A_ij Z_j,   Z_i ~= A_ii^{-1} T_i,
+with A_ij = sum_k G_k(i,j) K_k and A_ii = K_0 (G_k(i,i) = 0 for symmetric
+densities).  B_T^T is applied by backward substitution with A_ji^T.
+
+Diagonal solve options: a V-cycle (``Hierarchy.vcycle``) or the exact
+sparse LU of K_0 (used for the spectral checks of Sec. 5).
+"""
+import numpy as np
+import scipy.sparse.linalg as spla
+
+
+class DiagSolver:
+    def __init__(self, K0, hierarchy=None):
+        self.hier = hierarchy
+        self.lu = None if hierarchy is not None else spla.splu(K0.tocsc())
+
+    def __call__(self, b):
+        if self.hier is not None:
+            return self.hier.vcycle(b)
+        return self.lu.solve(b)
+
+
+def block_diag_inv(sys, solver, R):
+    """Z = B_D^{-1} R: every PC block solved with the mean operator K_0."""
+    Rm = np.asarray(R, dtype=np.float64).reshape(sys.P, sys.Nx)
+    Z = solver(Rm.T).T
+    return np.ascontiguousarray(Z).reshape(-1)
+
+
+def _offdiag_block_apply(sys, i, j, Zj, transpose=False):
+    """A_ij Zj (or A_ji^T Zj) for i != j, skipping zero Kronecker factors."""
+    out = None
+    for k in range(1, sys.M + 1):
+        g = sys.G[k][j, i] if transpose else sys.G[k][i, j]
+        if g != 0.0:
+            Kk = sys.K[k].T if transpose else sys.K[k]
+            t = g * (Kk @ Zj)
+            out = t if out is None else out + t
+    return out
+
+
+def block_tri_inv(sys, solver, R, transpose=False):
+    """Z = B_T^{-1} R (forward substitution) or B_T^{-T} R (backward substitution)."""
+    Rm = np.asarray(R, dtype=np.float64).reshape(sys.P, sys.Nx)
+    Z = np.zeros_like(Rm)
+    order = range(sys.P - 1, -1, -1) if transpose else range(sys.P)
+    for i in order:
+        T = Rm[i].copy()
+        others = range(i + 1, sys.P) if transpose else range(i)
+        for j in others:
+            c = _offdiag_block_apply(sys, i, j, Z[j], transpose)
+            if c is not None:
+                T -= c
+        Z[i] = solver(T)
+    return Z.reshape(-1)

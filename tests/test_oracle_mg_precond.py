@@ -1,0 +1,152 @@
+"""Pins of the oracle's multigrid V-cycle (Sec. 4.1) and block preconditioners
+(Sec. 4.1-4.2) against closed forms, brute-force dense solves and the spectral
+results of Sec. 5 (Lemmas 1-2, Theorems 1-2, the ideal Schur remark)."""
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+from oracle import basis, fem, kl, mg, precond, sg
+
+
+def _system(n=9, M=2, p=3, sigma=0.3, family=basis.LEGENDRE):
+    return sg.build(n, M, p, family, kl.kl_coefficients(n, M, sigma))
+
+
+def _vcycle_matrix(h):
+    N = h.A[0].shape[0]
+    return h.vcycle(np.eye(N))
+
+
+def test_jacobi_smoothing_factor_is_one_third():
+    """Damped Jacobi, omega = 8/9, on the Q1 stencil: max |1 - omega lambda / d| over the
+    high-frequency eigenmodes (max(j,k) >= (n-1)/2) equals 1/3 (closed-form spectrum)."""
+    n = 65
+    h = 1.0 / (n - 1)
+    j = np.arange(1, n - 1)
+    c = np.cos(j * np.pi * h)
+    J, K = np.meshgrid(j, j)
+    cj, ck = np.meshgrid(c, c)
+    lam = (2.0 / 3.0) * (4 - cj - ck - 2 * cj * ck)
+    hf = np.maximum(J, K) >= (n - 1) // 2
+    amp = np.abs(1 - (8.0 / 9.0) * lam[hf] / (8.0 / 3.0))
+    assert abs(amp.max() - 1.0 / 3.0) < 1e-3 and amp.max() <= 1.0 / 3.0 + 1e-12
+    # and the oracle's hierarchy uses that diagonal on every level for abar = 1
+    hier = mg.Hierarchy(fem.assemble_stiffness(17, np.ones(256)), 17)
+    for d in hier.Dinv:
+        assert np.allclose(d, 3.0 / 8.0)
+
+
+def test_vcycle_symmetric_and_contracting():
+    n = 17
+    K0 = fem.assemble_stiffness(n, np.ones((n - 1) ** 2))
+    hier = mg.Hierarchy(K0, n)
+    Mv = _vcycle_matrix(hier)
+    assert np.abs(Mv - Mv.T).max() < 1e-14
+    E = np.eye(Mv.shape[0]) - Mv @ K0.toarray()
+    rho = max(abs(np.linalg.eigvals(E)))
+    assert 0.02 < rho < 0.35          # sanity band (no closed form)
+
+
+def test_vcycle_variable_coefficient_galerkin():
+    n = 17
+    K0 = fem.assemble_stiffness(n, np.exp(0.2 * np.random.default_rng(2).standard_normal((n - 1) ** 2)))
+    hier = mg.Hierarchy(K0, n)
+    Mv = _vcycle_matrix(hier)
+    assert np.abs(Mv - Mv.T).max() < 1e-13
+    rho = max(abs(np.linalg.eigvals(np.eye(Mv.shape[0]) - Mv @ K0.toarray())))
+    assert rho < 0.4
+
+
+def _lower_block_triangular(A, P, Nx):
+    B = A.copy()
+    for i in range(P):
+        B[i * Nx:(i + 1) * Nx, (i + 1) * Nx:] = 0.0
+    return B
+
+
+def test_block_tri_forward_substitution_is_dense_solve():
+    s = _system(n=5, M=2, p=2)
+    A = sg.assemble(s).toarray()
+    B = _lower_block_triangular(A, s.P, s.Nx)
+    solver = precond.DiagSolver(s.K[0])
+    R = np.random.default_rng(0).standard_normal(s.P * s.Nx)
+    assert np.allclose(precond.block_tri_inv(s, solver, R), np.linalg.solve(B, R), atol=1e-12)
+    assert np.allclose(precond.block_tri_inv(s, solver, R, transpose=True), np.linalg.solve(B.T, R), atol=1e-12)
+    # diagonal blocks are exactly K_0
+    for i in range(s.P):
+        assert np.abs(A[i * s.Nx:(i + 1) * s.Nx, i * s.Nx:(i + 1) * s.Nx] - s.K[0].toarray()).max() == 0.0
+
+
+def test_block_diag_is_kron_identity_k0():
+    s = _system(n=5, M=2, p=2)
+    solver = precond.DiagSolver(s.K[0])
+    R = np.random.default_rng(1).standard_normal(s.P * s.Nx)
+    BD = np.kron(np.eye(s.P), s.K[0].toarray())
+    assert np.allclose(precond.block_diag_inv(s, solver, R), np.linalg.solve(BD, R), atol=1e-12)
+
+
+def _split(s):
+    A = sg.assemble(s).toarray()
+    Ph = basis.n_basis(s.M, s.p - 1) * s.Nx
+    return A, A[:Ph, :Ph], A[Ph:, :Ph], A[Ph:, Ph:]
+
+
+def test_lemma2_powell_elman_bound():
+    s = _system(n=17, M=4, p=1, sigma=0.3)
+    K0 = s.K[0].toarray()
+    sup = kl.kl_mode_sup(4)
+    lam = kl.kl_eigenvalues(4)
+    for k in range(1, 5):
+        ev = sla.eigh(s.K[k].toarray(), K0, eigvals_only=True)
+        assert np.abs(ev).max() <= np.abs(s.coef[k]).max() / s.coef[0].min() + 1e-12
+        assert np.abs(ev).max() <= 0.3 * math.sqrt(lam[k - 1]) * sup[k - 1] + 1e-12
+
+
+def test_theorem1_and_lemma1_two_by_two_split():
+    s = _system(n=9, M=2, p=3, sigma=0.4)
+    A, Ah, W, D = _split(s)
+    BT = np.block([[Ah, np.zeros_like(W.T)], [W, D]])
+    ev = np.linalg.eigvals(np.linalg.solve(BT, A))
+    assert np.abs(ev.imag).max() < 1e-8
+    assert ev.real.min() > 0 and ev.real.max() <= 1 + 1e-10
+    S = D - W @ np.linalg.solve(Ah, W.T)
+    mu = sla.eigh(S, D, eigvals_only=True)
+    for v in ev.real:
+        assert abs(v - 1) < 1e-8 or np.abs(mu - v).min() < 1e-8
+
+
+def test_theorem2_p1_lower_bound():
+    M, sigma = 4, 0.3
+    s = _system(n=17, M=M, p=1, sigma=sigma)
+    A, Ah, W, D = _split(s)
+    BT = np.block([[Ah, np.zeros_like(W.T)], [W, D]])
+    ev = np.linalg.eigvals(np.linalg.solve(BT, A)).real
+    bound = 1 - np.sum(sigma ** 2 * kl.kl_eigenvalues(M) * kl.kl_mode_sup(M) ** 2)
+    assert ev.min() >= bound - 1e-12
+    assert ev.min() < 1.0
+
+
+def test_recursive_block_tri_spectrum_consistently_ordered():
+    """A is block tridiagonal in degree levels, hence consistently ordered: the spectrum of the
+    recursive B_T^{-1} A (exact diagonal blocks) is {1 - mu^2 : mu in sigma(I - B_D^{-1} A)}."""
+    s = _system(n=9, M=2, p=3, sigma=0.3)
+    A = sg.assemble(s).toarray()
+    BT = _lower_block_triangular(A, s.P, s.Nx)
+    BD = np.kron(np.eye(s.P), s.K[0].toarray())
+    nu = np.linalg.eigvals(np.linalg.solve(BT, A))
+    mu = np.linalg.eigvals(np.eye(A.shape[0]) - np.linalg.solve(BD, A)).real
+    assert np.abs(nu.imag).max() < 1e-6
+    target = 1 - mu ** 2
+    for v in nu.real:
+        assert np.abs(target - v).min() < 1e-7 or abs(v - 1) < 1e-7
+    assert abs(nu.real.min() - (1 - mu.max() ** 2)) < 1e-8
+
+
+def test_ideal_schur_minimal_polynomial_degree_two():
+    s = _system(n=5, M=2, p=2, sigma=0.4)
+    A, Ah, W, D = _split(s)
+    S = D - W @ np.linalg.solve(Ah, W.T)
+    Bt = np.block([[Ah, np.zeros_like(W.T)], [W, S]])
+    E = np.linalg.solve(Bt, A) - np.eye(A.shape[0])
+    assert np.abs(E @ E).max() < 1e-12 * np.abs(E).max() + 1e-13
