@@ -1,0 +1,185 @@
+/*
+ * sg.h -- C ABI of the GB300 stochastic Galerkin (SG) solver.
+ *
+ * Method: Zheng, Lin and Xu, "Block Triangular Preconditioning for Stochastic
+ * Galerkin Method" (arXiv 1304.1755).  Problem (Sec. 2, Eq. model-problem):
+ *   -div(a(x, xi) grad u) = f on the unit square, u = 0 on the boundary,
+ *   a = abar(x) + sum_{k=1}^M sqrt(lambda_k) b_k(x) xi_k   (Eq. truncated-KLE),
+ * discretised by Q1 finite elements on a uniform (n x n)-vertex grid and a
+ * total-degree-p orthonormal polynomial chaos (Legendre or Hermite).  The
+ * Galerkin matrix is A = sum_{k=0}^M G_k (x) K_k (Eq. tensor-product); it is
+ * never assembled.
+ *
+ * Data layout of every SG vector (X, Y, R, Z, F, U):  PC-major,
+ *   V[i * N_x + s],  i = 0..P-1 (PC index, degree-graded), s = 0..N_x-1,
+ *   N_x = (n-2)^2 interior nodes, s = (vx-1) + (vy-1)(n-2) for vertex (vx, vy)
+ *   (x1 fastest).  P = (M+p)!/(M! p!).
+ * Element types: SG_F64 = double, SG_F32 = float, SG_BF16 = bfloat16 (raw
+ * uint16 bit pattern of the upper half of an IEEE float).
+ *
+ * Ownership: the caller owns every buffer passed in; the handle owns the
+ * operator data and all workspace (device memory, allocated at setup and on
+ * first use of a precision).  Calls are ordered on the handle's CUDA stream;
+ * functions that return host-visible results (sg_solve, sg_objective,
+ * sg_adjoint_gradients) synchronise that stream before returning.
+ * A handle is not thread-safe; distinct handles are independent.
+ *
+ * Errors: every function returns an sg_status (0 = success, negative =
+ * failure); no exception crosses the ABI.  sg_last_error() gives a message.
+ * After SG_E_CUDA the handle should be destroyed.
+ */
+#ifndef SG_GB300_H
+#define SG_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_ctx* sg_handle;
+
+typedef enum {
+  SG_OK = 0,
+  SG_E_ARG = -1,        /* invalid argument (sizes, pointers, options) */
+  SG_E_ALLOC = -2,      /* device or host allocation failed */
+  SG_E_CUDA = -3,       /* a CUDA runtime call failed */
+  SG_E_NOCONV = -4,     /* solver hit maxit before the tolerance */
+  SG_E_BREAKDOWN = -5,  /* Krylov breakdown (zero or non-positive pivot) */
+  SG_E_NONFINITE = -6,  /* NaN or Inf met in a residual or inner product */
+  SG_E_TIMEOUT = -7,    /* a bounded device-side wait gave up */
+  SG_E_STATE = -8       /* call not valid in the handle's current state */
+} sg_status;
+
+typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2 } sg_prec;
+typedef enum { SG_LEGENDRE = 0, SG_HERMITE = 1 } sg_family;
+typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3 } sg_method;
+typedef enum { SG_PC_NONE = 0, SG_PC_BLOCKTRI = 1, SG_PC_BLOCKDIAG = 2 } sg_pc;
+
+/* One SG problem (Sec. 2-3).  coef is a HOST array of (M+1) rows of (n-1)^2
+ * per-cell values, cell e = cx + cy (n-1): row 0 is the mean coefficient
+ * abar_e (defines K_0, Eq. def-stiffness), row k >= 1 is
+ * c_k(e) = sqrt(lambda_k) b_k(x_e) (times sigma), defining K_k.  The handle
+ * copies it.  n = 2^L + 1 with 3 <= n <= 4097; 0 <= M <= 16; 0 <= p <= 10;
+ * P <= 4096.  nu1, nu2: damped-Jacobi pre/post smoothing steps of the V-cycle
+ * (0 selects 1; at most 4); omega: Jacobi weight (0 selects 8/9). */
+typedef struct {
+  int n;
+  int M;
+  int p;
+  int family;
+  const double* coef;
+  int nu1;
+  int nu2;
+  double omega;
+} sg_problem;
+
+/* Solver options (Sec. 4.2, 6).  method: GMRES (right preconditioned) or
+ * FGMRES (flexible: stores z_j = B^{-1} v_j in pc_prec) or GPCG[1] or PCG.
+ * precond: block-triangular B_T, block-diagonal B_D or none.  restart: Krylov
+ * dimension m of (F)GMRES(m) (1..64).  maxit: maximum preconditioner
+ * applications.  tol: stop when ||F - A U||_2 / ||F||_2 <= tol (true residual,
+ * recomputed in FP64 at every restart and at the end).  pc_prec: precision of
+ * the preconditioner (V-cycle and triangular sweep); the outer Krylov vectors,
+ * orthogonalisation, Givens rotations, true residual and coarsest-grid solve
+ * are always FP64.  transpose: solve A^T U = F preconditioned by B^T (the
+ * adjoint solve; B_T^T is the upper block-triangular sweep).  x0_given: U holds
+ * an initial guess (else U = 0 is used).  reorth: 0 classical Gram-Schmidt,
+ * 1 classical Gram-Schmidt with a second pass when the norm drops by more than
+ * 1/sqrt(2) (selective reorthogonalisation). */
+typedef struct {
+  int method;
+  int precond;
+  int restart;
+  int maxit;
+  double tol;
+  int pc_prec;
+  int transpose;
+  int x0_given;
+  int reorth;
+} sg_solve_opts;
+
+/* Filled by sg_solve. iters = preconditioner applications (Arnoldi steps);
+ * relres_est = the recurrence's residual estimate; relres_true = recomputed
+ * ||F - A U|| / ||F|| in FP64; times are wall clock (ms) measured with CUDA
+ * events on the handle's stream. */
+typedef struct {
+  int iters;
+  int restarts;
+  int status;
+  double relres_est;
+  double relres_true;
+  double t_total_ms;
+  int n_apply;
+  int n_precond;
+} sg_solve_info;
+
+/* Host helper (Sec. 2.1, Eqs. truncated-KLE and exponential-covariance):
+ * fills coef_out ((M+1) x (n-1)^2, host) with row 0 = abar (or 1 where abar is
+ * NULL) and row k = sigma sqrt(lambda_k) b_k(cell centre) for the separable
+ * covariance exp(-|x1-y1|/L - |x2-y2|/L), L = corr_len, modes sorted by
+ * decreasing lambda (ties: lower x1-mode index first).  lambda_out (host, M
+ * values) may be NULL.  Pure host computation, no device use. */
+int sg_kl_coef(int n, int M, double sigma, double corr_len, const double* abar,
+               double* coef_out, double* lambda_out);
+
+/* Build a handle: uploads coefficients, basis tables and the multigrid
+ * hierarchy (Galerkin coarse stencils when abar is not constant 1).  stream is
+ * a cudaStream_t (NULL = legacy default stream). */
+int sg_setup(const sg_problem* prob, void* stream, sg_handle* out);
+void sg_destroy(sg_handle h);
+int sg_set_stream(sg_handle h, void* stream);
+const char* sg_last_error(sg_handle h);   /* h may be NULL: last setup error */
+
+/* Sizes: N_x, P, number of multigrid levels (each may be NULL). */
+int sg_sizes(sg_handle h, int* Nx, int* P, int* nlevels);
+/* Multi-indices of the PC basis (host array P x M, row i = alpha_i),
+ * degree-graded order (Sec. 3.3). */
+int sg_basis(sg_handle h, int* alpha);
+
+/* Y = A X (Eq. tensor-product), device X, Y in precision prec; arithmetic in
+ * FP64 for SG_F64, FP32 otherwise. */
+int sg_apply(sg_handle h, const void* X, void* Y, int prec);
+/* R = F - A U in FP64 (device F, U, R; R may alias F). */
+int sg_residual(sg_handle h, const double* F, const double* U, double* R);
+
+/* Z = B_T^{-1} R (Sec. 4.2): block forward substitution over the degree
+ * levels q = 0..p, each diagonal block K_0 approximated by one V-cycle; with
+ * transpose != 0, Z = B_T^{-T} R (backward over q = p..0).  R is FP64 (device),
+ * Z is in precision prec (device); intermediate storage in prec. */
+int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose);
+/* Z = B_D^{-1} R (Sec. 4.1): one V-cycle on every PC block. */
+int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec);
+/* One V(nu1,nu2) cycle on K_0 from a zero guess for nblocks stacked blocks of
+ * N_x values: B FP64 (device), X in prec (device). */
+int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec);
+
+/* Solve A U = F (or A^T U = F).  F, U: FP64, host or device pointers (host
+ * buffers are staged through device memory inside the call).  info may be
+ * NULL.  Returns SG_E_NOCONV if maxit is reached (U then holds the last
+ * iterate). */
+int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info);
+
+/* Objective J = E[Q] + Var[Q]/2, Q = int u dx: J = m^T U_0 + 1/2 sum_{i>=1}(m^T U_i)^2
+ * with m_s = h^2, and its gradient G = dJ/dU (device U, G; J host). */
+int sg_objective(sg_handle h, const double* U, double* J, double* G);
+/* Adjoint gradients: g_abar[e] = -sum_i Lam_i|e^T K_ref U_i|e (dJ/dabar per
+ * cell, device, (n-1)^2 values) and *g_sigma = -(1/sigma) Lam^T (A - I (x) K_0) U
+ * (host), given the forward solution U and the adjoint Lam (device FP64). */
+int sg_adjoint_gradients(sg_handle h, const double* U, const double* Lam, double sigma,
+                         double* g_abar, double* g_sigma);
+
+/* Tracing (no counterpart in the paper): per-phase device time measured with
+ * CUDA events recorded on the handle's stream around the kernels of each phase
+ * of sg_solve.  Phases: 0 = outer operator A z (FP64), 1 = preconditioner
+ * (sweep + V-cycles), 2 = Gram-Schmidt kernels, 3 = other vector kernels.
+ * sg_timing_enable(h, 1) starts a fresh accumulation (0 stops recording).
+ * sg_timing_read synchronises the stream and writes the accumulated ms[4] and
+ * kernel-launch counts launches[4] since the last enable/read (either pointer
+ * may be NULL), then resets them.  Kernel launches are counted whether or not
+ * timing is enabled. */
+int sg_timing_enable(sg_handle h, int enable);
+int sg_timing_read(sg_handle h, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

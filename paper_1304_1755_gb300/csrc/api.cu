@@ -1,0 +1,576 @@
+// C-ABI entry points: set-up, operator, preconditioners and the Krylov drivers
+// (Sec. 4.2: GMRES / flexible GMRES / GPCG[1] / PCG around B_T or B_D).
+// The Krylov loops run on the host; every vector operation runs in this
+// library's kernels and only scalars (Hessenberg columns, norms) cross to the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sg_internal.h"
+
+namespace {
+std::string g_setup_err;
+std::mutex g_err_mu;
+
+template <typename T>
+int upload(sg_ctx* h, T** dst, const T* src, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc(dst, sizeof(T) * count) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "device allocation failed");
+  SG_CUDA(h, cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+  return SG_OK;
+}
+
+int upload_terms(sg_ctx* h, TermTable& T, int which) {
+  std::vector<int> rp, tj, tk;
+  std::vector<double> tg;
+  build_terms(h, which, rp, tj, tk, tg);
+  T.nnz = (int)tj.size();
+  if (tj.empty()) { tj.push_back(0); tk.push_back(0); tg.push_back(0.0); }
+  std::vector<float> tgf(tg.begin(), tg.end());
+  int rc;
+  if ((rc = upload(h, &T.row_ptr, rp.data(), rp.size()))) return rc;
+  if ((rc = upload(h, &T.j, tj.data(), tj.size()))) return rc;
+  if ((rc = upload(h, &T.k, tk.data(), tk.size()))) return rc;
+  if ((rc = upload(h, &T.g, tg.data(), tg.size()))) return rc;
+  if ((rc = upload(h, &T.gf, tgf.data(), tgf.size()))) return rc;
+  return SG_OK;
+}
+
+void free_terms(TermTable& T) {
+  cudaFree(T.row_ptr), cudaFree(T.j), cudaFree(T.k), cudaFree(T.g), cudaFree(T.gf);
+  T = TermTable{};
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+double host_dot(sg_ctx* h, const double* x, const double* y, size_t N, int* rc) {
+  const double* xs[1] = {x};
+  const void* ys[1] = {y};
+  int yp[1] = {SG_F64};
+  double out = 0;
+  *rc = vec_dot_pairs(h, 1, xs, ys, yp, N, &out);
+  return out;
+}
+
+int apply_precond(sg_ctx* h, int pc, const double* R, void* Z, int prec, int transpose) {
+  if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, R, Z, prec, transpose);
+  if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, R, Z, prec);
+  return vec_cast(h, SG_F64, R, prec, Z, h->Nx * (size_t)h->P);
+}
+
+int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec) {
+  const size_t N = h->Nx * (size_t)h->P;
+  if (h->kv_cap < nv) {
+    cudaFree(h->kv);
+    h->kv = nullptr;
+    h->kv_cap = 0;
+    if (cudaMalloc(&h->kv, sizeof(double) * N * nv) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc Krylov basis");
+    h->kv_cap = nv;
+  }
+  if (h->kz_cap < nz || h->kz_prec != zprec) {
+    cudaFree(h->kz);
+    h->kz = nullptr;
+    h->kz_cap = 0;
+    if (cudaMalloc(&h->kz, prec_size(zprec) * N * std::max(nz, 1)) != cudaSuccess)
+      return sg_fail(h, SG_E_ALLOC, "alloc preconditioned basis");
+    h->kz_cap = std::max(nz, 1);
+    h->kz_prec = zprec;
+  }
+  if (!h->ktmp && cudaMalloc(&h->ktmp, sizeof(double) * N * 4) != cudaSuccess)
+    return sg_fail(h, SG_E_ALLOC, "alloc work vectors");
+  return ensure_reduction(h);
+}
+
+// ---------------------------------------------------------------------------
+// Restarted right-preconditioned GMRES / FGMRES (Saad-Schultz; Sec. 4.2, 6).
+int solve_gmres(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info, bool flexible) {
+  const size_t N = h->Nx * (size_t)h->P;
+  const int m = o.restart;
+  const int zp = o.pc_prec;
+  int rc = ensure_krylov(h, m + 1, flexible ? m : 1, zp);
+  if (rc) return rc;
+  const size_t zs = prec_size(zp);
+  double* V = h->kv;
+  const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
+  if (rc) return rc;
+  if (!std::isfinite(bnorm)) return sg_fail(h, SG_E_NONFINITE, "non-finite right-hand side");
+  if (bnorm == 0.0) {
+    SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream));
+    info.relres_true = info.relres_est = 0;
+    return SG_OK;
+  }
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), h2(m + 2), y(m);
+  int its = 0;
+  for (;;) {
+    rc = launch_apply(h, 0, SG_F64, U, SG_F64, V, F, 0, h->P, 0, 0, 1);   // V_0 = F - A U
+    if (rc) return rc;
+    const double beta = std::sqrt(host_dot(h, V, V, N, &rc));
+    if (rc) return rc;
+    if (!std::isfinite(beta)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
+    info.relres_true = beta / bnorm;
+    if (beta <= o.tol * bnorm) { info.relres_est = info.relres_true; break; }
+    if (its >= o.maxit) { info.iters = its; return SG_E_NOCONV; }
+    if ((rc = vec_scale(h, V, V, N, 1.0 / beta))) return rc;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      void* zj = (char*)h->kz + zs * N * (flexible ? j : 0);
+      double* w = V + N * (j + 1);
+      {
+        PhaseScope ps(h, 1);
+        if ((rc = apply_precond(h, o.precond, V + N * j, zj, zp, o.transpose))) return rc;
+      }
+      {
+        PhaseScope ps(h, 0);
+        if ((rc = launch_apply(h, 0, zp, zj, SG_F64, w, nullptr, 0, h->P, 0, 0, 1))) return rc;   // w = A z_j
+      }
+      // classical Gram-Schmidt: h = V^T w (with w.w), w -= V h, ||w||^2
+      {
+        PhaseScope ps(h, 2);
+        if ((rc = vec_dots(h, V, N, j + 1, w, N, true, nullptr))) return rc;
+      }
+      if ((rc = copy_red(h, 0, j + 2, hcol.data()))) return rc;
+      double nrm2 = 0;
+      {
+        PhaseScope ps(h, 2);
+        if ((rc = vec_axpys_norm(h, V, N, j + 1, h->red_out, w, N, nullptr))) return rc;
+      }
+      if ((rc = copy_red(h, 1, 1, &nrm2))) return rc;
+      if (o.reorth && nrm2 < 0.5 * hcol[j + 1]) {
+        {
+          PhaseScope ps(h, 2);
+          if ((rc = vec_dots(h, V, N, j + 1, w, N, false, nullptr))) return rc;
+        }
+        if ((rc = copy_red(h, 0, j + 1, h2.data()))) return rc;
+        {
+          PhaseScope ps(h, 2);
+          if ((rc = vec_axpys_norm(h, V, N, j + 1, h->red_out, w, N, nullptr))) return rc;
+        }
+        if ((rc = copy_red(h, 1, 1, &nrm2))) return rc;
+        for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
+      }
+      const double hn = std::sqrt(nrm2);
+      for (int i = 0; i <= j; ++i) {
+        if (!std::isfinite(hcol[i])) return sg_fail(h, SG_E_NONFINITE, "non-finite Hessenberg entry");
+        H[i * m + j] = hcol[i];
+      }
+      if (!std::isfinite(hn)) return sg_fail(h, SG_E_NONFINITE, "non-finite Arnoldi norm");
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double d = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      if (d == 0.0) return sg_fail(h, SG_E_BREAKDOWN, "GMRES breakdown (zero Hessenberg column)");
+      cs[j] = H[j * m + j] / d;
+      sn[j] = H[(j + 1) * m + j] / d;
+      H[j * m + j] = d;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      info.relres_est = std::fabs(g[j + 1]) / bnorm;
+      if (hn == 0.0 || std::fabs(g[j + 1]) <= o.tol * bnorm || its >= o.maxit) break;
+      if ((rc = vec_scale(h, w, w, N, 1.0 / hn))) return rc;
+    }
+    for (int i = k - 1; i >= 0; --i) {   // back substitution H y = g
+      double s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
+      y[i] = s / H[i * m + i];
+    }
+    if (flexible) {
+      if ((rc = vec_update(h, U, zp, h->kz, N, k, y.data(), N))) return rc;
+    } else {
+      double* t = h->ktmp;
+      SG_CUDA(h, cudaMemsetAsync(t, 0, sizeof(double) * N, h->stream));
+      if ((rc = vec_update(h, t, SG_F64, V, N, k, y.data(), N))) return rc;
+      if ((rc = apply_precond(h, o.precond, t, h->kz, zp, o.transpose))) return rc;
+      if ((rc = vec_axpy_prec(h, 1.0, zp, h->kz, U, N))) return rc;
+    }
+    info.restarts++;
+  }
+  info.iters = its;
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// GPCG[1] (Sec. 4.2, 6): g = B^{-1} r, A-orthogonalise against the previous
+// direction, alpha = <r,d>/<Ad,d>.
+int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
+  const size_t N = h->Nx * (size_t)h->P;
+  const int zp = o.pc_prec;
+  int rc = ensure_krylov(h, 1, 1, zp);
+  if (rc) return rc;
+  double *r = h->ktmp, *Ag = h->ktmp + N, *d = h->ktmp + 2 * N, *Ad = h->ktmp + 3 * N;
+  void* gv = h->kz;
+  const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
+  if (rc) return rc;
+  if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  if ((rc = launch_apply(h, 0, SG_F64, U, SG_F64, r, F, 0, h->P, 0, 0, 1))) return rc;
+  double rr = host_dot(h, r, r, N, &rc);
+  if (rc) return rc;
+  double Add_prev = 0;
+  int its = 0;
+  while (std::sqrt(rr) > o.tol * bnorm) {
+    if (!std::isfinite(rr)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
+    if (its >= o.maxit) { info.iters = its; info.relres_true = std::sqrt(rr) / bnorm; return SG_E_NOCONV; }
+    if ((rc = apply_precond(h, o.precond, r, gv, zp, o.transpose))) return rc;
+    if ((rc = launch_apply(h, 0, zp, gv, SG_F64, Ag, nullptr, 0, h->P, 0, 0, 1))) return rc;
+    if (its == 0) {
+      if ((rc = vec_cast(h, zp, gv, SG_F64, d, N))) return rc;
+      SG_CUDA(h, cudaMemcpyAsync(Ad, Ag, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      const double beta = host_dot(h, Ag, d, N, &rc) / Add_prev;
+      if (rc) return rc;
+      if ((rc = vec_axpby(h, 0.0, d, -beta, d, N))) return rc;        // d = -beta d
+      if ((rc = vec_axpy_prec(h, 1.0, zp, gv, d, N))) return rc;      // d += g
+      if ((rc = vec_axpby(h, 1.0, Ag, -beta, Ad, N))) return rc;      // Ad = Ag - beta Ad
+    }
+    const double* xs[2] = {r, Ad};
+    const void* ys[2] = {d, d};
+    int yp[2] = {SG_F64, SG_F64};
+    double dd[2];
+    if ((rc = vec_dot_pairs(h, 2, xs, ys, yp, N, dd))) return rc;
+    if (!(dd[1] > 0) && !(dd[1] < 0)) return sg_fail(h, SG_E_BREAKDOWN, "GPCG breakdown (<Ad,d> = 0)");
+    const double alpha = dd[0] / dd[1];
+    Add_prev = dd[1];
+    if ((rc = vec_axpby(h, alpha, d, 1.0, U, N))) return rc;
+    if ((rc = vec_axpby(h, -alpha, Ad, 1.0, r, N))) return rc;
+    rr = host_dot(h, r, r, N, &rc);
+    if (rc) return rc;
+    ++its;
+  }
+  info.iters = its;
+  info.relres_est = std::sqrt(rr) / bnorm;
+  return SG_OK;
+}
+
+// Standard PCG (Sec. 4.2, with B_D or the SPD B_S); B_T is accepted but not SPD.
+int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
+  const size_t N = h->Nx * (size_t)h->P;
+  const int zp = o.pc_prec;
+  int rc = ensure_krylov(h, 1, 1, zp);
+  if (rc) return rc;
+  double *r = h->ktmp, *Ad = h->ktmp + N, *d = h->ktmp + 2 * N;
+  void* z = h->kz;
+  const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
+  if (rc) return rc;
+  if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  if ((rc = launch_apply(h, 0, SG_F64, U, SG_F64, r, F, 0, h->P, 0, 0, 1))) return rc;
+  if ((rc = apply_precond(h, o.precond, r, z, zp, o.transpose))) return rc;
+  if ((rc = vec_cast(h, zp, z, SG_F64, d, N))) return rc;
+  const double* xs0[2] = {r, r};
+  const void* ys0[2] = {z, r};
+  int yp0[2] = {zp, SG_F64};
+  double t2[2];
+  if ((rc = vec_dot_pairs(h, 2, xs0, ys0, yp0, N, t2))) return rc;
+  double rz = t2[0], rr = t2[1];
+  int its = 0;
+  while (std::sqrt(rr) > o.tol * bnorm) {
+    if (!std::isfinite(rr)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
+    if (its >= o.maxit) { info.iters = its; info.relres_true = std::sqrt(rr) / bnorm; return SG_E_NOCONV; }
+    if ((rc = launch_apply(h, 0, SG_F64, d, SG_F64, Ad, nullptr, 0, h->P, 0, 0, 1))) return rc;
+    const double dAd = host_dot(h, d, Ad, N, &rc);
+    if (rc) return rc;
+    if (!(dAd > 0) && !(dAd < 0)) return sg_fail(h, SG_E_BREAKDOWN, "PCG breakdown (<d,Ad> = 0)");
+    const double alpha = rz / dAd;
+    if ((rc = vec_axpby(h, alpha, d, 1.0, U, N))) return rc;
+    if ((rc = vec_axpby(h, -alpha, Ad, 1.0, r, N))) return rc;
+    ++its;
+    if ((rc = apply_precond(h, o.precond, r, z, zp, o.transpose))) return rc;
+    if ((rc = vec_dot_pairs(h, 2, xs0, ys0, yp0, N, t2))) return rc;
+    const double beta = t2[0] / rz;
+    rz = t2[0], rr = t2[1];
+    if ((rc = vec_axpby(h, 0.0, d, beta, d, N))) return rc;           // d = beta d
+    if ((rc = vec_axpy_prec(h, 1.0, zp, z, d, N))) return rc;          // d += z
+  }
+  info.iters = its;
+  info.relres_est = std::sqrt(rr) / bnorm;
+  return SG_OK;
+}
+
+void destroy_ctx(sg_ctx* h) {
+  if (!h) return;
+  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->pvec);
+  free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off);
+  for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
+  for (auto& W : h->work) {
+    cudaFree(W.T);
+    for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(W.b[l]), cudaFree(W.x[l]);
+  }
+  cudaFree(h->red_partial), cudaFree(h->red_out), cudaFree(h->red_count), cudaFreeHost(h->red_host);
+  cudaFree(h->kv), cudaFree(h->kz), cudaFree(h->ktmp), cudaFree(h->dstage);
+  delete h;
+}
+}  // namespace
+
+int sg_fail(sg_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_setup_err = msg;
+  }
+  return code;
+}
+
+size_t prec_size(int prec) { return prec == SG_F64 ? 8 : (prec == SG_F32 ? 4 : 2); }
+
+extern "C" {
+
+int sg_kl_coef(int n, int M, double sigma, double corr_len, const double* abar, double* coef_out, double* lambda_out) {
+  if (n < 3 || M < 0 || M > 64 || !coef_out || !(corr_len > 0) || !std::isfinite(sigma))
+    return sg_fail(nullptr, SG_E_ARG, "sg_kl_coef: bad argument");
+  return kl_coef_host(n, M, sigma, corr_len, abar, coef_out, lambda_out);
+}
+
+const char* sg_last_error(sg_handle h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_setup_err.c_str();
+}
+
+int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
+  if (!prob || !out || !prob->coef) return sg_fail(nullptr, SG_E_ARG, "sg_setup: null argument");
+  *out = nullptr;
+  const int n = prob->n, M = prob->M, p = prob->p;
+  bool pow2 = n >= 3 && n <= 4097 && ((n - 1) & (n - 2)) == 0;
+  if (!pow2) return sg_fail(nullptr, SG_E_ARG, "sg_setup: n must be 2^L + 1 with 3 <= n <= 4097");
+  if (M < 0 || M > 16 || p < 0 || p > 10) return sg_fail(nullptr, SG_E_ARG, "sg_setup: need 0 <= M <= 16, 0 <= p <= 10");
+  if (prob->family != SG_LEGENDRE && prob->family != SG_HERMITE) return sg_fail(nullptr, SG_E_ARG, "sg_setup: bad family");
+  const int nu1 = prob->nu1 ? prob->nu1 : 1, nu2 = prob->nu2 ? prob->nu2 : 1;
+  if (nu1 < 1 || nu1 > 4 || nu2 < 1 || nu2 > 4) return sg_fail(nullptr, SG_E_ARG, "sg_setup: smoothing steps must be 1..4");
+  double Pd = 1;
+  for (int t = 1; t <= p; ++t) Pd = Pd * (M + t) / t;
+  if (Pd > 4096) return sg_fail(nullptr, SG_E_ARG, "sg_setup: P exceeds 4096");
+  sg_ctx* h = new sg_ctx();
+  h->n = n, h->m = n - 2, h->M = M, h->p = p, h->family = prob->family;
+  h->Nx = (size_t)h->m * h->m, h->Nc = (size_t)(n - 1) * (n - 1);
+  h->nu1 = nu1, h->nu2 = nu2;
+  h->omega = prob->omega > 0 ? prob->omega : 8.0 / 9.0;
+  h->stream = (cudaStream_t)stream;
+  build_basis(M, p, h->alpha, h->lvl_off);
+  h->P = h->lvl_off.back();
+  h->coef_h.assign(prob->coef, prob->coef + (size_t)(M + 1) * h->Nc);
+  for (double v : h->coef_h)
+    if (!std::isfinite(v)) { delete h; return sg_fail(nullptr, SG_E_ARG, "sg_setup: non-finite coefficient"); }
+  h->const_mean = true;
+  for (size_t e = 0; e < h->Nc; ++e)
+    if (h->coef_h[e] != 1.0) { h->const_mean = false; break; }
+  int rc;
+  std::vector<float> c32(h->coef_h.begin(), h->coef_h.end());
+  if ((rc = upload(h, &h->coef64, h->coef_h.data(), h->coef_h.size())) ||
+      (rc = upload(h, &h->coef32, c32.data(), c32.size())) || (rc = upload_terms(h, h->t_all, 0)) ||
+      (rc = upload_terms(h, h->t_lower, 1)) || (rc = upload_terms(h, h->t_upper, 2)) ||
+      (rc = upload_terms(h, h->t_off, 3))) {
+    std::string e = h->err;
+    destroy_ctx(h);
+    return sg_fail(nullptr, rc, "sg_setup: " + e);
+  }
+  if (cudaMalloc(&h->pvec, sizeof(double) * std::max(h->P, 64)) != cudaSuccess) {
+    destroy_ctx(h);
+    return sg_fail(nullptr, SG_E_ALLOC, "sg_setup: scratch allocation");
+  }
+  // multigrid hierarchy n_{l+1} = (n_l + 1) / 2 down to n = 3
+  h->nlev = 0;
+  for (int nl = n;; nl = (nl + 1) / 2) {
+    MGLevel& L = h->lev[h->nlev++];
+    L.n = nl, L.m = nl - 2, L.N = (size_t)L.m * L.m;
+    if (nl <= 3) break;
+  }
+  h->lc = 0;
+  while (h->lc < h->nlev && h->lev[h->lc].n > 33) ++h->lc;
+  if (!h->const_mean) {
+    std::vector<std::vector<double>> st;
+    galerkin_stencils(n, h->nlev, h->coef_h.data(), st);
+    for (int l = 0; l < h->nlev; ++l) {
+      std::vector<float> s32(st[l].begin(), st[l].end());
+      if ((rc = upload(h, &h->lev[l].st64, st[l].data(), st[l].size())) ||
+          (rc = upload(h, &h->lev[l].st32, s32.data(), s32.size()))) {
+        std::string e = h->err;
+        destroy_ctx(h);
+        return sg_fail(nullptr, rc, "sg_setup: " + e);
+      }
+    }
+  }
+  *out = h;
+  return SG_OK;
+}
+
+void sg_destroy(sg_handle h) {
+  if (h && h->stream) cudaStreamSynchronize(h->stream);
+  destroy_ctx(h);
+}
+
+int sg_set_stream(sg_handle h, void* stream) {
+  if (!h) return SG_E_ARG;
+  h->stream = (cudaStream_t)stream;
+  return SG_OK;
+}
+
+int sg_sizes(sg_handle h, int* Nx, int* P, int* nlevels) {
+  if (!h) return SG_E_ARG;
+  if (Nx) *Nx = (int)h->Nx;
+  if (P) *P = h->P;
+  if (nlevels) *nlevels = h->nlev;
+  return SG_OK;
+}
+
+int sg_basis(sg_handle h, int* alpha) {
+  if (!h || !alpha) return SG_E_ARG;
+  std::copy(h->alpha.begin(), h->alpha.end(), alpha);
+  return SG_OK;
+}
+
+int sg_apply(sg_handle h, const void* X, void* Y, int prec) {
+  if (!h || !X || !Y || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_apply: bad argument") : SG_E_ARG;
+  return launch_apply(h, 0, prec, X, prec, Y, nullptr, 0, h->P, 0, 0, prec == SG_F64);
+}
+
+int sg_residual(sg_handle h, const double* F, const double* U, double* R) {
+  if (!h || !F || !U || !R) return h ? sg_fail(h, SG_E_ARG, "sg_residual: null argument") : SG_E_ARG;
+  if ((const void*)U == (const void*)R) return sg_fail(h, SG_E_ARG, "sg_residual: U must not alias R");
+  return launch_apply(h, 0, SG_F64, U, SG_F64, R, F, 0, h->P, 0, 0, 1);
+}
+
+int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose) {
+  if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocktri: bad argument") : SG_E_ARG;
+  return precond_blocktri(h, R, Z, prec, transpose != 0);
+}
+
+int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec) {
+  if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blockdiag: bad argument") : SG_E_ARG;
+  return precond_blockdiag(h, R, Z, prec);
+}
+
+int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
+  if (!h || !B || !X || prec < 0 || prec > 2 || nblocks < 0 || nblocks > h->P)
+    return h ? sg_fail(h, SG_E_ARG, "sg_vcycle: bad argument") : SG_E_ARG;
+  return vcycle_run(h, prec, nblocks, B, SG_F64, X);
+}
+
+int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info_out) {
+  if (!h || !F || !U || !opts) return h ? sg_fail(h, SG_E_ARG, "sg_solve: null argument") : SG_E_ARG;
+  sg_solve_opts o = *opts;
+  if (o.method < SG_GMRES || o.method > SG_PCG || o.precond < 0 || o.precond > 2 || o.pc_prec < 0 || o.pc_prec > 2 ||
+      !(o.tol > 0) || o.maxit < 0)
+    return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
+  if ((o.method == SG_GMRES || o.method == SG_FGMRES) && (o.restart < 1 || o.restart > 32))
+    return sg_fail(h, SG_E_ARG, "sg_solve: restart must be 1..32");
+  sg_solve_info info{};
+  const size_t N = h->Nx * (size_t)h->P;
+  const bool dev = is_device_ptr(F) && is_device_ptr(U);
+  const double* dF = F;
+  double* dU = U;
+  if (!dev) {
+    if (!h->dstage && cudaMalloc(&h->dstage, sizeof(double) * N * 2) != cudaSuccess)
+      return sg_fail(h, SG_E_ALLOC, "sg_solve: staging allocation");
+    SG_CUDA(h, cudaMemcpyAsync(h->dstage, F, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    dF = h->dstage;
+    dU = h->dstage + N;
+    if (o.x0_given) SG_CUDA(h, cudaMemcpyAsync(dU, U, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+  }
+  cudaEvent_t e0, e1;
+  SG_CUDA(h, cudaEventCreate(&e0));
+  SG_CUDA(h, cudaEventCreate(&e1));
+  SG_CUDA(h, cudaEventRecord(e0, h->stream));
+  if (!o.x0_given) SG_CUDA(h, cudaMemsetAsync(dU, 0, sizeof(double) * N, h->stream));
+  int rc;
+  if (o.method == SG_GMRES || o.method == SG_FGMRES) rc = solve_gmres(h, dF, dU, o, info, o.method == SG_FGMRES);
+  else if (o.method == SG_GPCG) rc = solve_gpcg(h, dF, dU, o, info);
+  else rc = solve_pcg(h, dF, dU, o, info);
+  if (rc == SG_OK || rc == SG_E_NOCONV) {
+    // true residual in FP64
+    int rc2 = ensure_krylov(h, 1, 1, o.pc_prec);
+    if (!rc2) rc2 = launch_apply(h, 0, SG_F64, dU, SG_F64, h->ktmp, dF, 0, h->P, 0, 0, 1);
+    double rr = 0, ff = 0;
+    if (!rc2) rr = host_dot(h, h->ktmp, h->ktmp, N, &rc2);
+    if (!rc2) ff = host_dot(h, dF, dF, N, &rc2);
+    if (rc2) rc = rc2;
+    else info.relres_true = ff > 0 ? std::sqrt(rr / ff) : 0.0;
+  }
+  if (!dev && (rc == SG_OK || rc == SG_E_NOCONV))
+    SG_CUDA(h, cudaMemcpyAsync(U, dU, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  SG_CUDA(h, cudaEventRecord(e1, h->stream));
+  SG_CUDA(h, cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0), cudaEventDestroy(e1);
+  info.t_total_ms = ms;
+  info.status = rc;
+  if (info_out) *info_out = info;
+  return rc;
+}
+
+int sg_timing_enable(sg_handle h, int enable) {
+  if (!h) return SG_E_ARG;
+  SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& s : h->tr.spans) h->tr.pool.push_back(s.a), h->tr.pool.push_back(s.b);
+  h->tr.spans.clear();
+  for (auto& l : h->tr.launches) l = 0;
+  h->tr.on = enable != 0;
+  return SG_OK;
+}
+
+int sg_timing_read(sg_handle h, double* ms, long long* launches) {
+  if (!h) return SG_E_ARG;
+  SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  double acc[4] = {0, 0, 0, 0};
+  for (auto& s : h->tr.spans) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, s.a, s.b) == cudaSuccess) acc[s.phase] += t;
+    else cudaGetLastError();
+    h->tr.pool.push_back(s.a), h->tr.pool.push_back(s.b);
+  }
+  h->tr.spans.clear();
+  if (ms) std::copy(acc, acc + 4, ms);
+  if (launches) std::copy(h->tr.launches, h->tr.launches + 4, launches);
+  for (auto& l : h->tr.launches) l = 0;
+  return SG_OK;
+}
+
+int sg_objective(sg_handle h, const double* U, double* J, double* G) {
+  if (!h || !U || !J) return h ? sg_fail(h, SG_E_ARG, "sg_objective: null argument") : SG_E_ARG;
+  std::vector<double> mu(h->P);
+  int rc = objective_dots(h, U, mu.data());
+  if (rc) return rc;
+  double j = mu[0];
+  for (int i = 1; i < h->P; ++i) j += 0.5 * mu[i] * mu[i];
+  *J = j;
+  if (G) {
+    if ((rc = objective_grad(h, h->pvec, G))) return rc;
+    SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return SG_OK;
+}
+
+int sg_adjoint_gradients(sg_handle h, const double* U, const double* Lam, double sigma, double* g_abar, double* g_sigma) {
+  if (!h || !U || !Lam) return h ? sg_fail(h, SG_E_ARG, "sg_adjoint_gradients: null argument") : SG_E_ARG;
+  int rc;
+  if (g_abar && (rc = adj_cell_forms(h, U, Lam, g_abar))) return rc;
+  if (g_sigma) {
+    if (!(sigma != 0.0)) return sg_fail(h, SG_E_ARG, "sg_adjoint_gradients: sigma must be nonzero");
+    if ((rc = ensure_krylov(h, 1, 1, SG_F64))) return rc;
+    // (A - I (x) K_0) U = sum_{k>=1} G_k (x) K_k U, linear in sigma
+    if ((rc = launch_apply(h, 3, SG_F64, U, SG_F64, h->ktmp, nullptr, 0, h->P, 0, 0, 1))) return rc;
+    const double d = host_dot(h, Lam, h->ktmp, h->Nx * (size_t)h->P, &rc);
+    if (rc) return rc;
+    *g_sigma = -d / sigma;
+  }
+  SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SG_OK;
+}
+
+}  // extern "C"

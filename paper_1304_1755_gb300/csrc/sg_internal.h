@@ -1,0 +1,182 @@
+// Internal declarations of the GB300 stochastic Galerkin library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sg.h"
+
+typedef __nv_bfloat16 bf16;
+
+#define SG_MAX_LEVELS 13
+#define SG_MAX_RESTART 64
+#define SG_NTHREADS_RED 256
+
+// Scalar load/store with conversion to the arithmetic type.
+template <typename TA, typename TS> __device__ __forceinline__ TA ld_as(const TS* p) { return (TA)(*p); }
+template <> __device__ __forceinline__ float ld_as<float, bf16>(const bf16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ double ld_as<double, bf16>(const bf16* p) { return (double)__bfloat162float(*p); }
+template <typename TS, typename TA> __device__ __forceinline__ void st_as(TS* p, TA v) { *p = (TS)v; }
+template <> __device__ __forceinline__ void st_as<bf16, float>(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ void st_as<bf16, double>(bf16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+
+// PC-coupling table in CSR form over rows: for row i the terms t in
+// [row_ptr[i], row_ptr[i+1]) contribute  g[t] * K_{k[t]} X_{j[t]}  to Y_i.
+struct TermTable {
+  int* row_ptr = nullptr;
+  int* j = nullptr;
+  int* k = nullptr;
+  double* g = nullptr;
+  float* gf = nullptr;
+  int nnz = 0;
+};
+
+// One multigrid level: vertex count n_l, interior side m_l = n_l - 2.
+struct MGLevel {
+  int n = 0, m = 0;
+  size_t N = 0;               // m * m
+  double* st64 = nullptr;     // 9 * N Galerkin stencil (only when the mean is not constant 1)
+  float* st32 = nullptr;
+};
+
+// Per-storage-precision multigrid and sweep buffers.
+struct PrecWork {
+  bool ready = false;
+  void* T = nullptr;                    // stage right-hand side, n_q_max * N_x
+  void* b[SG_MAX_LEVELS] = {};          // level >= 1 right-hand sides, P * N_l
+  void* x[SG_MAX_LEVELS] = {};          // level >= 1 solutions, P * N_l
+};
+
+// Per-phase event tracing (sg_timing_*).  Phase 0 outer operator, 1 preconditioner,
+// 2 Gram-Schmidt, 3 other.
+struct Tracer {
+  bool on = false;
+  struct Span { cudaEvent_t a, b; int phase; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Span> spans;
+  long long launches[4] = {0, 0, 0, 0};
+};
+
+struct sg_ctx {
+  // problem
+  int n = 0, m = 0, M = 0, p = 0, P = 0, family = 0;
+  size_t Nx = 0, Nc = 0;
+  int nu1 = 1, nu2 = 1;
+  double omega = 8.0 / 9.0;
+  bool const_mean = true;
+  cudaStream_t stream = nullptr;
+  std::vector<int> alpha;               // P * M
+  std::vector<int> lvl_off;             // p + 2 offsets of the degree levels
+  std::vector<double> coef_h;           // (M+1) * Nc
+  // device operator data
+  double* coef64 = nullptr;             // (M+1) * Nc
+  float* coef32 = nullptr;
+  TermTable t_all, t_lower, t_upper, t_off;   // all / lower / upper / off-diagonal couplings
+  double* pvec = nullptr;               // P doubles of device scratch (objective)
+  // multigrid hierarchy
+  int nlev = 0;
+  int lc = 0;                           // first level handled by the single-CTA coarse kernel
+  MGLevel lev[SG_MAX_LEVELS];
+  PrecWork work[3];
+  // Krylov workspace (allocated on first solve)
+  double* red_partial = nullptr;        // reduction partials
+  double* red_out = nullptr;            // reduction results (device)
+  unsigned* red_count = nullptr;
+  double* red_host = nullptr;           // pinned
+  int red_blocks = 0;
+  double* kv = nullptr;                 // (restart + 1) FP64 vectors
+  int kv_cap = 0;
+  void* kz = nullptr;                   // restart vectors in pc precision
+  int kz_cap = 0, kz_prec = -1;
+  double* ktmp = nullptr;               // 4 FP64 work vectors
+  double* dstage = nullptr;             // staging for host F/U (2 vectors)
+  Tracer tr;
+  int phase = 3;
+  std::string err;
+};
+
+inline void count_launch(sg_ctx* h, int k = 1) { h->tr.launches[h->phase] += k; }
+
+// Sets the current phase and, when tracing, brackets the enclosed launches with events.
+struct PhaseScope {
+  sg_ctx* h;
+  int prev;
+  cudaEvent_t b = nullptr;
+  PhaseScope(sg_ctx* h_, int ph) : h(h_), prev(h_->phase) {
+    h->phase = ph;
+    if (h->tr.on) {
+      cudaEvent_t a = take_event(h);
+      b = take_event(h);
+      cudaEventRecord(a, h->stream);
+      h->tr.spans.push_back({a, b, ph});
+    }
+  }
+  ~PhaseScope() {
+    if (b) cudaEventRecord(b, h->stream);
+    h->phase = prev;
+  }
+  static cudaEvent_t take_event(sg_ctx* h) {
+    if (h->tr.pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = h->tr.pool.back();
+    h->tr.pool.pop_back();
+    return e;
+  }
+};
+
+// error helpers
+int sg_fail(sg_ctx* h, int code, const std::string& msg);
+#define SG_CUDA(h, call)                                                          \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return sg_fail((h), SG_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t prec_size(int prec);
+
+// setup.cpp
+int kl_coef_host(int n, int M, double sigma, double corr_len, const double* abar, double* coef, double* lam);
+void build_basis(int M, int p, std::vector<int>& alpha, std::vector<int>& lvl_off);
+double gamma_1d(int family, int nn);
+void build_terms(const sg_ctx* h, int which, std::vector<int>& row_ptr, std::vector<int>& tj,
+                 std::vector<int>& tk, std::vector<double>& tg);
+void galerkin_stencils(int n0, int nlev, const double* abar_cells, std::vector<std::vector<double>>& st);
+
+// k_apply.cu
+// which: 0 = all terms (Y = A X), 1 = lower terms, 2 = upper terms, 3 = off-diagonal terms.
+// Computes Y_i (i in [row0, row0 + nrows)) = epi ? R_i - S_i : S_i,
+// S_i = sum over the table's terms; Y rows are offset by ybase, R rows by rbase.
+int launch_apply(sg_ctx* h, int which, int xprec, const void* X, int yprec, void* Y,
+                 const double* R, int row0, int nrows, int ybase, int rbase, int arith64);
+
+// k_mg.cu
+int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X);
+int ensure_prec_work(sg_ctx* h, int prec);
+int precond_blocktri(sg_ctx* h, const double* R, void* Z, int prec, int transpose);
+int precond_blockdiag(sg_ctx* h, const double* R, void* Z, int prec);
+
+// k_vec.cu
+int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host);
+int vec_axpys_norm(sg_ctx* h, const double* V, size_t ldv, int nv, const double* hcoef_dev, double* w, size_t N,
+                   double* nrm2_host);
+int vec_scale(sg_ctx* h, const double* w, double* v, size_t N, double s);
+int vec_update(sg_ctx* h, double* U, int zprec, const void* Z, size_t ldz, int nz, const double* y_host, size_t N);
+int vec_cast(sg_ctx* h, int iprec, const void* in, int oprec, void* out, size_t N);
+int vec_axpby(sg_ctx* h, double a, const double* x, double b, double* y, size_t N);   // y = a x + b y
+int vec_dot_pairs(sg_ctx* h, int npairs, const double* const* xs, const void* const* ys, const int* yprecs,
+                  size_t N, double* out_host);
+int vec_axpy_prec(sg_ctx* h, double a, int xprec, const void* x, double* y, size_t N);  // y += a x
+int ensure_reduction(sg_ctx* h);
+int copy_red(sg_ctx* h, int slot, int count, double* out_host);
+// adjoint helpers
+int adj_cell_forms(sg_ctx* h, const double* U, const double* L, double* g_abar);
+int objective_dots(sg_ctx* h, const double* U, double* mu_host);
+int objective_grad(sg_ctx* h, const double* mu_dev, double* G);

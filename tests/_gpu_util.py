@@ -1,0 +1,55 @@
+"""Helpers shared by the GPU parity tests: one SG problem built twice from the same
+seeded inputs -- once by the oracle (CPU, FP64) and once through the C ABI."""
+import numpy as np
+
+from oracle import basis, kl, mg, precond, sg as osg
+from paper_1304_1755_gb300 import inputs
+
+
+def coefficients(n, M, sigma=0.3, mean="one", seed=7):
+    """KL coefficients (from the oracle's own KL) with a constant, lognormal or random mean row."""
+    coef = kl.kl_coefficients(n, M, sigma)
+    if mean == "lognormal":
+        coef[0] = inputs.lognormal_cells(seed, n, 0.2)
+    elif mean == "random":
+        coef = inputs.random_cell_coefficients(seed, n, M, spread=0.2)
+    return coef
+
+
+class Pair:
+    def __init__(self, n, M, p, family=basis.LEGENDRE, sigma=0.3, mean="one", nu=(1, 1), seed=7, coef=None):
+        import torch
+        from paper_1304_1755_gb300 import sg
+        self.coef = coefficients(n, M, sigma, mean, seed) if coef is None else coef
+        self.sys = osg.build(n, M, p, family, self.coef)
+        self.h = sg.Handle(n, M, p, family, self.coef, nu1=nu[0], nu2=nu[1],
+                           stream=torch.cuda.current_stream())
+        self.nu = nu
+        assert self.h.P == self.sys.P and self.h.Nx == self.sys.Nx
+        self._hier = None
+
+    @property
+    def hier(self):
+        if self._hier is None:
+            self._hier = mg.Hierarchy(self.sys.K[0], self.sys.n, nu1=self.nu[0], nu2=self.nu[1])
+        return self._hier
+
+    @property
+    def N(self):
+        return self.sys.P * self.sys.Nx
+
+    def oracle_vsolver(self):
+        return precond.DiagSolver(self.sys.K[0], self.hier)
+
+
+def dev(x, dtype=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    import torch
+    return t.detach().to(torch.float64).cpu().numpy()

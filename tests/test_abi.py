@@ -1,0 +1,64 @@
+"""The C-ABI library loads, exports every function include/sg.h declares, and the
+Python binding covers them (CPU only: no device calls).  Also checks the host KL
+helper of the library against the oracle (pure host code)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sg.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(sg_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1304_1755_gb300 import build, sg
+    if not os.path.exists(sg.LIB_PATH):
+        build.build()
+    return sg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("sg_setup", "sg_apply", "sg_precond_blocktri", "sg_precond_blockdiag", "sg_solve"):
+        assert required in names
+    assert len(names) >= 15
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1304_1755_gb300 import sg
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert name in sg.SIGNATURES, name
+
+
+def test_null_arguments_rejected_without_device(lib):
+    from paper_1304_1755_gb300 import sg
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.sg_setup(None, None, ctypes.byref(h)) == -1
+    assert b"null" in lib.sg_last_error(None)
+    coef = np.ones((1, 16))
+    prob = sg.Problem(6, 0, 0, 0, coef.ctypes.data_as(sg.DP), 1, 1, 0.0)   # n = 6 is not 2^L + 1
+    assert lib.sg_setup(ctypes.byref(prob), None, ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("n,M,sigma", [(9, 2, 0.3), (33, 4, 0.5), (17, 6, 0.2)])
+def test_library_kl_helper_matches_oracle(lib, n, M, sigma):
+    from oracle import kl
+    from paper_1304_1755_gb300 import sg
+    coef, lam = sg.sg_kl_coef(n, M, sigma)
+    ref = kl.kl_coefficients(n, M, sigma)
+    assert np.allclose(coef, ref, rtol=0, atol=1e-13)
+    assert np.allclose(lam, kl.kl_eigenvalues(M), rtol=1e-13)
+    ab = np.linspace(0.5, 1.5, (n - 1) ** 2)
+    coef2, _ = sg.sg_kl_coef(n, M, sigma, abar=ab)
+    assert np.array_equal(coef2[0], ab)

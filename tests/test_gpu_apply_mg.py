@@ -1,0 +1,138 @@
+"""GPU parity: K1 (SG operator), the multigrid V-cycle and the block preconditioners
+against the oracle, element by element, through the C ABI.
+
+Tolerances (derived from the arithmetic):
+  * FP64 operator: every output is a short sum of products of the coefficients
+    and feature differences of X; the error is below ~50 ulp of the absolute
+    sum, so |Y - Y*| <= 2e-13 (|A| |X|) elementwise.
+  * FP32 arithmetic: the same bound with eps_32: 2e-5 (|A| |X|).
+  * BF16 storage of the output: plus 2^-8 |Y*| (round to nearest of the store).
+  * V-cycle / preconditioners (linear maps with O(1) amplification):
+    FP64 1e-11, FP32 1e-4 relative to max |Z*|; BF16 storage 3e-2 in the norm.
+"""
+import numpy as np
+import pytest
+
+from oracle import basis, precond, sg as osg
+from paper_1304_1755_gb300 import inputs
+from _gpu_util import Pair, dev, host
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # n, M, p, family, mean
+    (3, 1, 1, basis.LEGENDRE, "one"),
+    (5, 1, 0, basis.LEGENDRE, "one"),
+    (9, 2, 3, basis.HERMITE, "random"),
+    (33, 2, 2, basis.LEGENDRE, "one"),          # C1 shape
+    (65, 3, 3, basis.HERMITE, "lognormal"),
+    (129, 4, 2, basis.LEGENDRE, "one"),
+]
+
+
+def _abs_apply(sys, X):
+    import scipy.sparse as sp
+    A = osg.assemble(sys)
+    return abs(A) @ np.abs(X)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[0]}M{s[1]}p{s[2]}f{s[3]}{s[4]}")
+def test_apply_fp64(shape):
+    import torch
+    n, M, p, fam, mean = shape
+    pr = Pair(n, M, p, fam, mean=mean)
+    X = inputs.uniform(11, pr.N)
+    ref = osg.apply(pr.sys, X)
+    Y = torch.empty(pr.N, dtype=torch.float64, device="cuda")
+    pr.h.apply(dev(X), Y)
+    torch.cuda.synchronize()
+    bound = 2e-13 * _abs_apply(pr.sys, X) + 1e-300
+    assert np.all(np.abs(host(Y) - ref) <= bound)
+
+
+@pytest.mark.parametrize("shape", SHAPES[2:], ids=lambda s: f"n{s[0]}M{s[1]}p{s[2]}")
+@pytest.mark.parametrize("prec", [1, 2], ids=["f32", "bf16"])
+def test_apply_low_precision(shape, prec):
+    import torch
+    n, M, p, fam, mean = shape
+    pr = Pair(n, M, p, fam, mean=mean)
+    dt = torch.float32 if prec == 1 else torch.bfloat16
+    Xd = dev(inputs.uniform(12, pr.N), dt)
+    X = host(Xd)                          # the exactly representable input both sides use
+    ref = osg.apply(pr.sys, X)
+    Y = torch.empty(pr.N, dtype=dt, device="cuda")
+    pr.h.apply(Xd, Y, prec)
+    torch.cuda.synchronize()
+    bound = 2e-5 * _abs_apply(pr.sys, X) + (2.0 ** -8 * np.abs(ref) if prec == 2 else 0) + 1e-30
+    assert np.all(np.abs(host(Y) - ref) <= bound)
+
+
+def test_residual_fp64():
+    import torch
+    pr = Pair(33, 2, 2)
+    U = inputs.uniform(13, pr.N)
+    F = osg.rhs(pr.sys)
+    R = torch.empty(pr.N, dtype=torch.float64, device="cuda")
+    pr.h.residual(dev(F), dev(U), R)
+    torch.cuda.synchronize()
+    ref = F - osg.apply(pr.sys, U)
+    assert np.all(np.abs(host(R) - ref) <= 2e-13 * (_abs_apply(pr.sys, U) + np.abs(F)))
+
+
+MG_SHAPES = [(3, "one", (1, 1)), (5, "one", (1, 1)), (9, "random", (1, 1)), (33, "one", (1, 1)),
+             (65, "lognormal", (1, 1)), (129, "one", (1, 1)), (129, "lognormal", (2, 2)), (257, "one", (2, 1))]
+
+
+@pytest.mark.parametrize("n,mean,nu", MG_SHAPES, ids=lambda v: str(v))
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["f64", "f32", "bf16"])
+def test_vcycle(n, mean, nu, prec):
+    import torch
+    pr = Pair(n, 1, 2, mean=mean, nu=nu)      # P = 3 blocks of workspace
+    nb = 3
+    B = inputs.uniform(21, (nb, pr.sys.Nx))
+    ref = pr.hier.vcycle(B.T).T
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[prec]
+    X = torch.empty(nb * pr.sys.Nx, dtype=dt, device="cuda")
+    pr.h.vcycle(dev(B.reshape(-1)), X, nb, prec)
+    torch.cuda.synchronize()
+    got = host(X).reshape(nb, -1)
+    scale = np.abs(ref).max()
+    if prec == 0:
+        assert np.abs(got - ref).max() <= 1e-11 * scale
+    elif prec == 1:
+        assert np.abs(got - ref).max() <= 1e-4 * scale
+    else:
+        assert np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref)
+
+
+PC_SHAPES = [(9, 2, 3, basis.LEGENDRE, "one"), (33, 2, 2, basis.LEGENDRE, "one"),
+             (65, 3, 2, basis.HERMITE, "lognormal"), (129, 2, 3, basis.LEGENDRE, "one")]
+
+
+@pytest.mark.parametrize("shape", PC_SHAPES, ids=lambda s: f"n{s[0]}M{s[1]}p{s[2]}{s[4]}")
+@pytest.mark.parametrize("kind", ["tri", "tri_T", "diag"])
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["f64", "f32", "bf16"])
+def test_preconditioners(shape, kind, prec):
+    import torch
+    n, M, p, fam, mean = shape
+    pr = Pair(n, M, p, fam, mean=mean)
+    R = inputs.uniform(31, pr.N)
+    solver = pr.oracle_vsolver()
+    if kind == "diag":
+        ref = precond.block_diag_inv(pr.sys, solver, R)
+    else:
+        ref = precond.block_tri_inv(pr.sys, solver, R, transpose=(kind == "tri_T"))
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[prec]
+    Z = torch.empty(pr.N, dtype=dt, device="cuda")
+    if kind == "diag":
+        pr.h.precond_blockdiag(dev(R), Z, prec)
+    else:
+        pr.h.precond_blocktri(dev(R), Z, prec, transpose=(kind == "tri_T"))
+    torch.cuda.synchronize()
+    got = host(Z)
+    scale = np.abs(ref).max()
+    if prec == 0:
+        assert np.abs(got - ref).max() <= 1e-11 * scale
+    elif prec == 1:
+        assert np.abs(got - ref).max() <= 1e-4 * scale
+    else:
+        assert np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref)
