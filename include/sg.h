@@ -49,7 +49,19 @@ typedef enum {
   SG_E_STATE = -8       /* call not valid in the handle's current state */
 } sg_status;
 
-typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2 } sg_prec;
+/* SG_DF64: "double-float" storage of an N-element vector as 2N floats, the
+ * leading parts hi[0..N) followed by the trailing parts lo[N..2N), value
+ * hi + lo (about 48 significant bits).  It is the internal FP64-class format
+ * of the fast solver mode (GB300 runs FP64 arithmetic at 1/68 of its FP32
+ * rate); sg_apply accepts it for X and Y. */
+typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2, SG_DF64 = 3 } sg_prec;
+/* Arithmetic of the outer Krylov solver: SG_ARITH_F64 = IEEE FP64 throughout;
+ * SG_ARITH_DF64 = the Arnoldi basis, the outer operator A z and the
+ * Gram-Schmidt sums in double-float (FP32 pairs with error-free
+ * transformations), the Givens/least-squares update on the host in FP64 and
+ * the final true residual recomputed in IEEE FP64 (FGMRES only; the
+ * preconditioner must then be SG_F32 or SG_BF16). */
+typedef enum { SG_ARITH_F64 = 0, SG_ARITH_DF64 = 1 } sg_arith;
 typedef enum { SG_LEGENDRE = 0, SG_HERMITE = 1 } sg_family;
 typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3 } sg_method;
 typedef enum { SG_PC_NONE = 0, SG_PC_BLOCKTRI = 1, SG_PC_BLOCKDIAG = 2 } sg_pc;
@@ -84,7 +96,7 @@ typedef struct {
  * adjoint solve; B_T^T is the upper block-triangular sweep).  x0_given: U holds
  * an initial guess (else U = 0 is used).  reorth: 0 classical Gram-Schmidt,
  * 1 classical Gram-Schmidt with a second pass when the norm drops by more than
- * 1/sqrt(2) (selective reorthogonalisation). */
+ * 1/sqrt(2) (selective reorthogonalisation).  arith: sg_arith. */
 typedef struct {
   int method;
   int precond;
@@ -95,6 +107,7 @@ typedef struct {
   int transpose;
   int x0_given;
   int reorth;
+  int arith;
 } sg_solve_opts;
 
 /* Filled by sg_solve. iters = preconditioner applications (Arnoldi steps);
@@ -136,7 +149,7 @@ int sg_sizes(sg_handle h, int* Nx, int* P, int* nlevels);
 int sg_basis(sg_handle h, int* alpha);
 
 /* Y = A X (Eq. tensor-product), device X, Y in precision prec; arithmetic in
- * FP64 for SG_F64, FP32 otherwise. */
+ * FP64 for SG_F64, double-float for SG_DF64, FP32 otherwise. */
 int sg_apply(sg_handle h, const void* X, void* Y, int prec);
 /* R = F - A U in FP64 (device F, U, R; R may alias F). */
 int sg_residual(sg_handle h, const double* F, const double* U, double* R);

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "df64.cuh"
 #include "sg_internal.h"
 
 namespace {
@@ -30,18 +31,29 @@ int upload_terms(sg_ctx* h, TermTable& T, int which) {
   T.nnz = (int)tj.size();
   if (tj.empty()) { tj.push_back(0); tk.push_back(0); tg.push_back(0.0); }
   std::vector<float> tgf(tg.begin(), tg.end());
+  std::vector<float> tgd;
+  for (double v : tg) {
+    const df2 d = df_from_double(v);
+    tgd.push_back(d.hi), tgd.push_back(d.lo);
+  }
   int rc;
   if ((rc = upload(h, &T.row_ptr, rp.data(), rp.size()))) return rc;
   if ((rc = upload(h, &T.j, tj.data(), tj.size()))) return rc;
   if ((rc = upload(h, &T.k, tk.data(), tk.size()))) return rc;
   if ((rc = upload(h, &T.g, tg.data(), tg.size()))) return rc;
   if ((rc = upload(h, &T.gf, tgf.data(), tgf.size()))) return rc;
+  if ((rc = upload(h, &T.gdf, tgd.data(), tgd.size()))) return rc;
   return SG_OK;
 }
 
 void free_terms(TermTable& T) {
-  cudaFree(T.row_ptr), cudaFree(T.j), cudaFree(T.k), cudaFree(T.g), cudaFree(T.gf);
+  cudaFree(T.row_ptr), cudaFree(T.j), cudaFree(T.k), cudaFree(T.g), cudaFree(T.gf), cudaFree(T.gdf);
   T = TermTable{};
+}
+
+// FP64 operator on all rows: Y = A X (R == nullptr) or Y = R - A X, R FP64
+int apply_f64(sg_ctx* h, int which, int xprec, const void* X, int yprec, void* Y, const double* R) {
+  return launch_apply(h, which, xprec, X, 0, yprec, Y, 0, SG_F64, R, 0, 0, h->P, 0, 0, SG_F64);
 }
 
 bool is_device_ptr(const void* p) {
@@ -62,19 +74,22 @@ double host_dot(sg_ctx* h, const double* x, const double* y, size_t N, int* rc) 
   return out;
 }
 
-int apply_precond(sg_ctx* h, int pc, const double* R, void* Z, int prec, int transpose) {
-  if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, R, Z, prec, transpose);
-  if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, R, Z, prec);
-  return vec_cast(h, SG_F64, R, prec, Z, h->Nx * (size_t)h->P);
+int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec, int transpose) {
+  if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, rprec, R, Z, prec, transpose);
+  if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, rprec, R, Z, prec);
+  return vec_cast(h, rprec, R, prec, Z, h->Nx * (size_t)h->P);
 }
 
+// Krylov vectors use the padded length Np (multiple of 64) with zero padding, so the
+// Gram-Schmidt kernels can run 16-byte loads over whole vectors.
 int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec) {
-  const size_t N = h->Nx * (size_t)h->P;
+  const size_t N = h->Nx * (size_t)h->P, Np = h->Np;
   if (h->kv_cap < nv) {
     cudaFree(h->kv);
     h->kv = nullptr;
     h->kv_cap = 0;
-    if (cudaMalloc(&h->kv, sizeof(double) * N * nv) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc Krylov basis");
+    if (cudaMalloc(&h->kv, sizeof(double) * Np * nv) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc Krylov basis");
+    SG_CUDA(h, cudaMemsetAsync(h->kv, 0, sizeof(double) * Np * nv, h->stream));
     h->kv_cap = nv;
   }
   if (h->kz_cap < nz || h->kz_prec != zprec) {
@@ -86,76 +101,173 @@ int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec) {
     h->kz_cap = std::max(nz, 1);
     h->kz_prec = zprec;
   }
-  if (!h->ktmp && cudaMalloc(&h->ktmp, sizeof(double) * N * 4) != cudaSuccess)
-    return sg_fail(h, SG_E_ALLOC, "alloc work vectors");
+  if (!h->ktmp) {
+    if (cudaMalloc(&h->ktmp, sizeof(double) * Np * 4) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc work vectors");
+    SG_CUDA(h, cudaMemsetAsync(h->ktmp, 0, sizeof(double) * Np * 4, h->stream));
+  }
   return ensure_reduction(h);
 }
 
 // ---------------------------------------------------------------------------
 // Restarted right-preconditioned GMRES / FGMRES (Saad-Schultz; Sec. 4.2, 6).
-int solve_gmres(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info, bool flexible) {
-  const size_t N = h->Nx * (size_t)h->P;
+// The Arnoldi / Givens / restart logic is shared; the vector storage and
+// arithmetic come from an Ops class: OpsF64 (IEEE FP64 basis) or OpsDF (double-float
+// basis, FGMRES only).  Ops::v(l) is basis vector l; reductions land in the
+// reduction slots (0: Gram-Schmidt coefficients, 1: squared norm).
+struct OpsF64 {
+  sg_ctx* h;
+  const sg_solve_opts& o;
+  size_t N;
+  const double* F;
+  double* U;
+  bool flexible;
+  double* V;
+  int init() {
+    int rc = ensure_krylov(h, o.restart + 1, flexible ? o.restart : 1, o.pc_prec);
+    V = h->kv;
+    return rc;
+  }
+  double* v(int l) { return V + h->Np * l; }
+  void* z(int j) { return (char*)h->kz + prec_size(o.pc_prec) * N * (flexible ? j : 0); }
+  int norm2_rhs(double* out) { int rc; *out = host_dot(h, F, F, N, &rc); return rc; }
+  int zero_solution() { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  int residual(bool) { return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F); }
+  int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
+  int scale(int l, double s) { return vec_scale(h, v(l), v(l), N, s); }
+  int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
+  int apply(int j) { return apply_f64(h, 0, o.pc_prec, z(j), SG_F64, v(j + 1), nullptr); }
+  int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
+  int axpys(int j) { return vec_axpys_norm(h, V, h->Np, j + 1, h->red_out, v(j + 1), h->Np, nullptr); }
+  int update(int k, const double* y) {
+    if (flexible) return vec_update(h, U, o.pc_prec, h->kz, N, k, y, N);
+    double* t = h->ktmp;
+    SG_CUDA(h, cudaMemsetAsync(t, 0, sizeof(double) * N, h->stream));
+    int rc;
+    if ((rc = vec_update(h, t, SG_F64, V, h->Np, k, y, N))) return rc;
+    if ((rc = apply_precond(h, o.precond, SG_F64, t, h->kz, o.pc_prec, o.transpose))) return rc;
+    return vec_axpy_prec(h, 1.0, o.pc_prec, h->kz, U, N);
+  }
+  int finish() { return SG_OK; }
+};
+
+struct OpsDF {
+  sg_ctx* h;
+  const sg_solve_opts& o;
+  size_t N;
+  const double* F;
+  double* U;
+  float* V;    // vector l: hi at V + 2 Np l, lo at + Np
+  float* Fd;   // right-hand side and solution in double-float
+  float* Ud;
+  int init() {
+    if (o.pc_prec != SG_F32 && o.pc_prec != SG_BF16)
+      return sg_fail(h, SG_E_ARG, "double-float mode needs an FP32 or BF16 preconditioner");
+    int rc = ensure_krylov(h, o.restart + 1, o.restart, o.pc_prec);
+    if (rc) return rc;
+    const size_t Np = h->Np;
+    V = (float*)h->kv;
+    Fd = (float*)h->ktmp;
+    Ud = (float*)(h->ktmp + Np);
+    if ((rc = df_from_f64(h, F, Fd, N, Np))) return rc;
+    if (o.x0_given) return df_from_f64(h, U, Ud, N, Np);
+    SG_CUDA(h, cudaMemsetAsync(Ud, 0, sizeof(float) * 2 * Np, h->stream));
+    return SG_OK;
+  }
+  float* v(int l) { return V + 2 * h->Np * l; }
+  void* z(int j) { return (char*)h->kz + prec_size(o.pc_prec) * N * j; }
+  int norm2_rhs(double* out) {
+    int rc;
+    if ((rc = df_dots(h, nullptr, 0, 0, Fd, h->Np, true))) return rc;
+    return copy_red(h, 0, 1, out);
+  }
+  int zero_solution() { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  int residual(bool u_zero) {
+    const size_t Np = h->Np;
+    if (u_zero) {
+      SG_CUDA(h, cudaMemcpyAsync(v(0), Fd, sizeof(float) * 2 * Np, cudaMemcpyDeviceToDevice, h->stream));
+      return SG_OK;
+    }
+    return launch_apply(h, 0, SG_DF64, Ud, Np, SG_DF64, v(0), Np, SG_DF64, Fd, Np, 0, h->P, 0, 0, SG_DF64);
+  }
+  int norm2(int l, double* out) {
+    int rc;
+    if ((rc = df_dots(h, nullptr, 0, 0, v(l), h->Np, true))) return rc;
+    return copy_red(h, 0, 1, out);
+  }
+  int scale(int l, double s) { return df_scale(h, v(l), h->Np, s); }
+  int precond(int j) { return apply_precond(h, o.precond, SG_F32, v(j), z(j), o.pc_prec, o.transpose); }
+  int apply(int j) {
+    return launch_apply(h, 0, o.pc_prec, z(j), 0, SG_DF64, v(j + 1), h->Np, SG_DF64, nullptr, 0, 0, h->P, 0, 0,
+                        SG_DF64);
+  }
+  int dots(int j, bool ww) { return df_dots(h, V, 2 * h->Np, j + 1, v(j + 1), h->Np, ww); }
+  int axpys(int j) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, h->red_out, v(j + 1), h->Np); }
+  int update(int k, const double* y) { return df_update(h, Ud, h->Np, o.pc_prec, h->kz, N, k, y, N); }
+  int finish() { return df_to_f64(h, Ud, U, N, h->Np); }
+};
+
+template <class Ops>
+int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& info) {
   const int m = o.restart;
-  const int zp = o.pc_prec;
-  int rc = ensure_krylov(h, m + 1, flexible ? m : 1, zp);
+  int rc = ops.init();
   if (rc) return rc;
-  const size_t zs = prec_size(zp);
-  double* V = h->kv;
-  const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
-  if (rc) return rc;
+  double bb = 0;
+  if ((rc = ops.norm2_rhs(&bb))) return rc;
+  const double bnorm = std::sqrt(bb);
   if (!std::isfinite(bnorm)) return sg_fail(h, SG_E_NONFINITE, "non-finite right-hand side");
   if (bnorm == 0.0) {
-    SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream));
     info.relres_true = info.relres_est = 0;
-    return SG_OK;
+    return ops.zero_solution();
   }
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), h2(m + 2), y(m);
   int its = 0;
+  bool u_zero = !o.x0_given;
   for (;;) {
-    rc = launch_apply(h, 0, SG_F64, U, SG_F64, V, F, 0, h->P, 0, 0, 1);   // V_0 = F - A U
-    if (rc) return rc;
-    const double beta = std::sqrt(host_dot(h, V, V, N, &rc));
-    if (rc) return rc;
+    {
+      PhaseScope ps(h, 0);
+      if ((rc = ops.residual(u_zero))) return rc;   // v_0 = F - A U
+    }
+    double b2 = 0;
+    if ((rc = ops.norm2(0, &b2))) return rc;
+    const double beta = std::sqrt(b2);
     if (!std::isfinite(beta)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
     info.relres_true = beta / bnorm;
     if (beta <= o.tol * bnorm) { info.relres_est = info.relres_true; break; }
-    if (its >= o.maxit) { info.iters = its; return SG_E_NOCONV; }
-    if ((rc = vec_scale(h, V, V, N, 1.0 / beta))) return rc;
+    if (its >= o.maxit) { info.iters = its; ops.finish(); return SG_E_NOCONV; }
+    if ((rc = ops.scale(0, 1.0 / beta))) return rc;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      void* zj = (char*)h->kz + zs * N * (flexible ? j : 0);
-      double* w = V + N * (j + 1);
       {
         PhaseScope ps(h, 1);
-        if ((rc = apply_precond(h, o.precond, V + N * j, zj, zp, o.transpose))) return rc;
+        if ((rc = ops.precond(j))) return rc;                  // z_j = B^{-1} v_j
       }
       {
         PhaseScope ps(h, 0);
-        if ((rc = launch_apply(h, 0, zp, zj, SG_F64, w, nullptr, 0, h->P, 0, 0, 1))) return rc;   // w = A z_j
+        if ((rc = ops.apply(j))) return rc;                    // w = A z_j  (stored in v_{j+1})
       }
       // classical Gram-Schmidt: h = V^T w (with w.w), w -= V h, ||w||^2
       {
         PhaseScope ps(h, 2);
-        if ((rc = vec_dots(h, V, N, j + 1, w, N, true, nullptr))) return rc;
+        if ((rc = ops.dots(j, true))) return rc;
       }
       if ((rc = copy_red(h, 0, j + 2, hcol.data()))) return rc;
       double nrm2 = 0;
       {
         PhaseScope ps(h, 2);
-        if ((rc = vec_axpys_norm(h, V, N, j + 1, h->red_out, w, N, nullptr))) return rc;
+        if ((rc = ops.axpys(j))) return rc;
       }
       if ((rc = copy_red(h, 1, 1, &nrm2))) return rc;
       if (o.reorth && nrm2 < 0.5 * hcol[j + 1]) {
         {
           PhaseScope ps(h, 2);
-          if ((rc = vec_dots(h, V, N, j + 1, w, N, false, nullptr))) return rc;
+          if ((rc = ops.dots(j, false))) return rc;
         }
         if ((rc = copy_red(h, 0, j + 1, h2.data()))) return rc;
         {
           PhaseScope ps(h, 2);
-          if ((rc = vec_axpys_norm(h, V, N, j + 1, h->red_out, w, N, nullptr))) return rc;
+          if ((rc = ops.axpys(j))) return rc;
         }
         if ((rc = copy_red(h, 1, 1, &nrm2))) return rc;
         for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
@@ -184,26 +296,33 @@ int solve_gmres(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, s
       k = j + 1;
       info.relres_est = std::fabs(g[j + 1]) / bnorm;
       if (hn == 0.0 || std::fabs(g[j + 1]) <= o.tol * bnorm || its >= o.maxit) break;
-      if ((rc = vec_scale(h, w, w, N, 1.0 / hn))) return rc;
+      if ((rc = ops.scale(j + 1, 1.0 / hn))) return rc;
     }
     for (int i = k - 1; i >= 0; --i) {   // back substitution H y = g
       double s = g[i];
       for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
       y[i] = s / H[i * m + i];
     }
-    if (flexible) {
-      if ((rc = vec_update(h, U, zp, h->kz, N, k, y.data(), N))) return rc;
-    } else {
-      double* t = h->ktmp;
-      SG_CUDA(h, cudaMemsetAsync(t, 0, sizeof(double) * N, h->stream));
-      if ((rc = vec_update(h, t, SG_F64, V, N, k, y.data(), N))) return rc;
-      if ((rc = apply_precond(h, o.precond, t, h->kz, zp, o.transpose))) return rc;
-      if ((rc = vec_axpy_prec(h, 1.0, zp, h->kz, U, N))) return rc;
+    {
+      PhaseScope ps(h, 3);
+      if ((rc = ops.update(k, y.data()))) return rc;
     }
+    u_zero = false;
     info.restarts++;
   }
   info.iters = its;
-  return SG_OK;
+  return ops.finish();
+}
+
+int solve_gmres(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info, bool flexible) {
+  const size_t N = h->Nx * (size_t)h->P;
+  if (o.arith == SG_ARITH_DF64) {
+    if (!flexible) return sg_fail(h, SG_E_ARG, "double-float mode is implemented for FGMRES");
+    OpsDF ops{h, o, N, F, U, nullptr, nullptr, nullptr};
+    return solve_gmres_t(h, ops, o, info);
+  }
+  OpsF64 ops{h, o, N, F, U, flexible, nullptr};
+  return solve_gmres_t(h, ops, o, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -219,7 +338,7 @@ int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg
   const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
   if (rc) return rc;
   if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
-  if ((rc = launch_apply(h, 0, SG_F64, U, SG_F64, r, F, 0, h->P, 0, 0, 1))) return rc;
+  if ((rc = apply_f64(h,0, SG_F64, U, SG_F64, r, F))) return rc;
   double rr = host_dot(h, r, r, N, &rc);
   if (rc) return rc;
   double Add_prev = 0;
@@ -227,8 +346,8 @@ int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg
   while (std::sqrt(rr) > o.tol * bnorm) {
     if (!std::isfinite(rr)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
     if (its >= o.maxit) { info.iters = its; info.relres_true = std::sqrt(rr) / bnorm; return SG_E_NOCONV; }
-    if ((rc = apply_precond(h, o.precond, r, gv, zp, o.transpose))) return rc;
-    if ((rc = launch_apply(h, 0, zp, gv, SG_F64, Ag, nullptr, 0, h->P, 0, 0, 1))) return rc;
+    if ((rc = apply_precond(h, o.precond, SG_F64,r, gv, zp, o.transpose))) return rc;
+    if ((rc = apply_f64(h,0, zp, gv, SG_F64, Ag, nullptr))) return rc;
     if (its == 0) {
       if ((rc = vec_cast(h, zp, gv, SG_F64, d, N))) return rc;
       SG_CUDA(h, cudaMemcpyAsync(Ad, Ag, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
@@ -269,8 +388,8 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
   const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
   if (rc) return rc;
   if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
-  if ((rc = launch_apply(h, 0, SG_F64, U, SG_F64, r, F, 0, h->P, 0, 0, 1))) return rc;
-  if ((rc = apply_precond(h, o.precond, r, z, zp, o.transpose))) return rc;
+  if ((rc = apply_f64(h,0, SG_F64, U, SG_F64, r, F))) return rc;
+  if ((rc = apply_precond(h, o.precond, SG_F64,r, z, zp, o.transpose))) return rc;
   if ((rc = vec_cast(h, zp, z, SG_F64, d, N))) return rc;
   const double* xs0[2] = {r, r};
   const void* ys0[2] = {z, r};
@@ -282,7 +401,7 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
   while (std::sqrt(rr) > o.tol * bnorm) {
     if (!std::isfinite(rr)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
     if (its >= o.maxit) { info.iters = its; info.relres_true = std::sqrt(rr) / bnorm; return SG_E_NOCONV; }
-    if ((rc = launch_apply(h, 0, SG_F64, d, SG_F64, Ad, nullptr, 0, h->P, 0, 0, 1))) return rc;
+    if ((rc = apply_f64(h,0, SG_F64, d, SG_F64, Ad, nullptr))) return rc;
     const double dAd = host_dot(h, d, Ad, N, &rc);
     if (rc) return rc;
     if (!(dAd > 0) && !(dAd < 0)) return sg_fail(h, SG_E_BREAKDOWN, "PCG breakdown (<d,Ad> = 0)");
@@ -290,7 +409,7 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
     if ((rc = vec_axpby(h, alpha, d, 1.0, U, N))) return rc;
     if ((rc = vec_axpby(h, -alpha, Ad, 1.0, r, N))) return rc;
     ++its;
-    if ((rc = apply_precond(h, o.precond, r, z, zp, o.transpose))) return rc;
+    if ((rc = apply_precond(h, o.precond, SG_F64,r, z, zp, o.transpose))) return rc;
     if ((rc = vec_dot_pairs(h, 2, xs0, ys0, yp0, N, t2))) return rc;
     const double beta = t2[0] / rz;
     rz = t2[0], rr = t2[1];
@@ -304,7 +423,7 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
 
 void destroy_ctx(sg_ctx* h) {
   if (!h) return;
-  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->pvec);
+  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->pvec);
   free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off);
   for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
   for (auto& W : h->work) {
@@ -326,7 +445,7 @@ int sg_fail(sg_ctx* h, int code, const std::string& msg) {
   return code;
 }
 
-size_t prec_size(int prec) { return prec == SG_F64 ? 8 : (prec == SG_F32 ? 4 : 2); }
+size_t prec_size(int prec) { return (prec == SG_F64 || prec == SG_DF64) ? 8 : (prec == SG_F32 ? 4 : 2); }
 
 extern "C" {
 
@@ -363,6 +482,7 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
   h->stream = (cudaStream_t)stream;
   build_basis(M, p, h->alpha, h->lvl_off);
   h->P = h->lvl_off.back();
+  h->Np = (h->Nx * (size_t)h->P + 63) / 64 * 64;
   h->coef_h.assign(prob->coef, prob->coef + (size_t)(M + 1) * h->Nc);
   for (double v : h->coef_h)
     if (!std::isfinite(v)) { delete h; return sg_fail(nullptr, SG_E_ARG, "sg_setup: non-finite coefficient"); }
@@ -371,8 +491,15 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
     if (h->coef_h[e] != 1.0) { h->const_mean = false; break; }
   int rc;
   std::vector<float> c32(h->coef_h.begin(), h->coef_h.end());
+  std::vector<float> cdf;
+  cdf.reserve(2 * h->coef_h.size());
+  for (double v : h->coef_h) {
+    const df2 d = df_from_double(v);
+    cdf.push_back(d.hi), cdf.push_back(d.lo);
+  }
   if ((rc = upload(h, &h->coef64, h->coef_h.data(), h->coef_h.size())) ||
-      (rc = upload(h, &h->coef32, c32.data(), c32.size())) || (rc = upload_terms(h, h->t_all, 0)) ||
+      (rc = upload(h, &h->coef32, c32.data(), c32.size())) || (rc = upload(h, &h->coefdf, cdf.data(), cdf.size())) ||
+      (rc = upload_terms(h, h->t_all, 0)) ||
       (rc = upload_terms(h, h->t_lower, 1)) || (rc = upload_terms(h, h->t_upper, 2)) ||
       (rc = upload_terms(h, h->t_off, 3))) {
     std::string e = h->err;
@@ -435,24 +562,26 @@ int sg_basis(sg_handle h, int* alpha) {
 }
 
 int sg_apply(sg_handle h, const void* X, void* Y, int prec) {
-  if (!h || !X || !Y || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_apply: bad argument") : SG_E_ARG;
-  return launch_apply(h, 0, prec, X, prec, Y, nullptr, 0, h->P, 0, 0, prec == SG_F64);
+  if (!h || !X || !Y || prec < 0 || prec > 3) return h ? sg_fail(h, SG_E_ARG, "sg_apply: bad argument") : SG_E_ARG;
+  const size_t lo = prec == SG_DF64 ? h->Nx * (size_t)h->P : 0;
+  const int arith = (prec == SG_F64 || prec == SG_DF64) ? prec : SG_F32;
+  return launch_apply(h, 0, prec, X, lo, prec, Y, lo, SG_F64, nullptr, 0, 0, h->P, 0, 0, arith);
 }
 
 int sg_residual(sg_handle h, const double* F, const double* U, double* R) {
   if (!h || !F || !U || !R) return h ? sg_fail(h, SG_E_ARG, "sg_residual: null argument") : SG_E_ARG;
   if ((const void*)U == (const void*)R) return sg_fail(h, SG_E_ARG, "sg_residual: U must not alias R");
-  return launch_apply(h, 0, SG_F64, U, SG_F64, R, F, 0, h->P, 0, 0, 1);
+  return apply_f64(h,0, SG_F64, U, SG_F64, R, F);
 }
 
 int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose) {
   if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocktri: bad argument") : SG_E_ARG;
-  return precond_blocktri(h, R, Z, prec, transpose != 0);
+  return precond_blocktri(h, SG_F64, R, Z, prec, transpose != 0);
 }
 
 int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec) {
   if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blockdiag: bad argument") : SG_E_ARG;
-  return precond_blockdiag(h, R, Z, prec);
+  return precond_blockdiag(h, SG_F64, R, Z, prec);
 }
 
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
@@ -469,6 +598,9 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
     return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
   if ((o.method == SG_GMRES || o.method == SG_FGMRES) && (o.restart < 1 || o.restart > 32))
     return sg_fail(h, SG_E_ARG, "sg_solve: restart must be 1..32");
+  if (o.arith != SG_ARITH_F64 && o.arith != SG_ARITH_DF64) return sg_fail(h, SG_E_ARG, "sg_solve: bad arith");
+  if (o.arith == SG_ARITH_DF64 && (o.method != SG_FGMRES || o.pc_prec == SG_F64))
+    return sg_fail(h, SG_E_ARG, "sg_solve: double-float mode needs FGMRES with an FP32 or BF16 preconditioner");
   sg_solve_info info{};
   const size_t N = h->Nx * (size_t)h->P;
   const bool dev = is_device_ptr(F) && is_device_ptr(U);
@@ -494,7 +626,7 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
   if (rc == SG_OK || rc == SG_E_NOCONV) {
     // true residual in FP64
     int rc2 = ensure_krylov(h, 1, 1, o.pc_prec);
-    if (!rc2) rc2 = launch_apply(h, 0, SG_F64, dU, SG_F64, h->ktmp, dF, 0, h->P, 0, 0, 1);
+    if (!rc2) rc2 = apply_f64(h,0, SG_F64, dU, SG_F64, h->ktmp, dF);
     double rr = 0, ff = 0;
     if (!rc2) rr = host_dot(h, h->ktmp, h->ktmp, N, &rc2);
     if (!rc2) ff = host_dot(h, dF, dF, N, &rc2);
@@ -564,7 +696,7 @@ int sg_adjoint_gradients(sg_handle h, const double* U, const double* Lam, double
     if (!(sigma != 0.0)) return sg_fail(h, SG_E_ARG, "sg_adjoint_gradients: sigma must be nonzero");
     if ((rc = ensure_krylov(h, 1, 1, SG_F64))) return rc;
     // (A - I (x) K_0) U = sum_{k>=1} G_k (x) K_k U, linear in sigma
-    if ((rc = launch_apply(h, 3, SG_F64, U, SG_F64, h->ktmp, nullptr, 0, h->P, 0, 0, 1))) return rc;
+    if ((rc = apply_f64(h,3, SG_F64, U, SG_F64, h->ktmp, nullptr))) return rc;
     const double d = host_dot(h, Lam, h->ktmp, h->Nx * (size_t)h->P, &rc);
     if (rc) return rc;
     *g_sigma = -d / sigma;

@@ -19,196 +19,10 @@
 #include <algorithm>
 
 #include "sg_internal.h"
+#include "mg_kernels.cuh"
 
 namespace {
-constexpr int MAXNU = 4;
-constexpr int CT = 16;                                   // coarse tile of mg_down
-constexpr int DW = 2 * CT + 1 + 2 * MAXNU;               // its fine window
-constexpr int UX = 32, UY = 16;                          // fine tile of mg_up
-constexpr int UH = 2 * MAXNU - 1;
-constexpr int UWX = UX + 2 * UH, UWY = UY + 2 * UH;
-constexpr int UCX = (UX + 2 * MAXNU) / 2 + 3, UCY = (UY + 2 * MAXNU) / 2 + 3;
 constexpr int NC0 = 33;                                  // levels with n <= NC0 run in mg_coarse
-
-template <typename TA> struct Q1 {
-  static __device__ __forceinline__ TA diag() { return TA(8) / TA(3); }
-};
-
-// A x at window point (li, lj) of a row-major window of width w.
-template <typename TA, bool VAR>
-__device__ __forceinline__ TA apply_pt(const TA* x, int w, int li, int lj, const TA* st) {
-  const TA* r0 = x + (lj - 1) * w + li;
-  const TA* r1 = r0 + w;
-  const TA* r2 = r1 + w;
-  if (VAR) {
-    return st[0] * r0[-1] + st[1] * r0[0] + st[2] * r0[1] + st[3] * r1[-1] + st[4] * r1[0] + st[5] * r1[1] +
-           st[6] * r2[-1] + st[7] * r2[0] + st[8] * r2[1];
-  }
-  const TA s9 = (r0[-1] + r0[0] + r0[1]) + (r1[-1] + r1[0] + r1[1]) + (r2[-1] + r2[0] + r2[1]);
-  return TA(3) * r1[0] - s9 * (TA(1) / TA(3));
-}
-
-template <typename TA, bool VAR>
-__device__ __forceinline__ TA dinv_at(const TA* st) {
-  if (VAR) return TA(1) / st[4];
-  return TA(3) / TA(8);
-}
-
-// ---------------------------------------------------------------------------
-template <typename TB, typename TS, typename TA, bool VAR>
-__global__ void __launch_bounds__(256) mg_down(const TB* __restrict__ b, TS* __restrict__ bc, int m, int mc,
-                                               size_t ldb, size_t ldc, const TA* __restrict__ st, TA omega,
-                                               int nu1, int tiles_x) {
-  __shared__ TA sb[DW * DW], sx0[DW * DW], sx1[DW * DW];
-  const int tile = blockIdx.x, blk = blockIdx.y;
-  const int I0 = (tile % tiles_x) * CT, J0 = (tile / tiles_x) * CT;
-  const int W = 2 * CT + 1 + 2 * nu1;
-  const int fi0 = 2 * I0 - nu1, fj0 = 2 * J0 - nu1;     // fine interior index of window (0,0)
-  const TB* bb = b + (size_t)blk * ldb;
-  for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
-    const int li = t % W, lj = t / W, i = fi0 + li, j = fj0 + lj;
-    TA v = 0, xv = 0;
-    if (i >= 0 && i < m && j >= 0 && j < m) {
-      v = ld_as<TA>(bb + (size_t)i + (size_t)j * m);
-      const TA* sp = VAR ? st + 9 * ((size_t)i + (size_t)j * m) : nullptr;
-      xv = omega * dinv_at<TA, VAR>(sp) * v;
-    }
-    sb[t] = v;
-    sx0[t] = xv;
-  }
-  __syncthreads();
-  TA* xc = sx0;
-  TA* xn = sx1;
-  for (int s = 2; s <= nu1; ++s) {
-    const int lo = s - 1, hi = W - (s - 1);
-    for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
-      const int li = t % W, lj = t / W, i = fi0 + li, j = fj0 + lj;
-      TA v = 0;
-      if (li >= lo && li < hi && lj >= lo && lj < hi && i >= 0 && i < m && j >= 0 && j < m) {
-        const TA* sp = VAR ? st + 9 * ((size_t)i + (size_t)j * m) : nullptr;
-        v = xc[t] + omega * dinv_at<TA, VAR>(sp) * (sb[t] - apply_pt<TA, VAR>(xc, W, li, lj, sp));
-      }
-      xn[t] = v;
-    }
-    __syncthreads();
-    TA* tmp = xc; xc = xn; xn = tmp;
-  }
-  // residual on the inner (2 CT + 1)^2 window, written over a second buffer
-  {
-    const int lo = nu1, hi = W - nu1;
-    for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
-      const int li = t % W, lj = t / W, i = fi0 + li, j = fj0 + lj;
-      TA r = 0;
-      if (li >= lo && li < hi && lj >= lo && lj < hi && i >= 0 && i < m && j >= 0 && j < m) {
-        const TA* sp = VAR ? st + 9 * ((size_t)i + (size_t)j * m) : nullptr;
-        r = sb[t] - apply_pt<TA, VAR>(xc, W, li, lj, sp);
-      }
-      xn[t] = r;
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < CT * CT; t += blockDim.x) {
-    const int I = I0 + t % CT, J = J0 + t / CT;
-    if (I < mc && J < mc) {
-      const int li = 2 * I - fi0, lj = 2 * J - fj0;        // window index of fine node 2I (weight 1/2)
-      const TA* r0 = xn + lj * W + li;
-      const TA* r1 = r0 + W;
-      const TA* r2 = r1 + W;
-      const TA v = TA(0.25) * (r0[0] + r0[2] + r2[0] + r2[2]) + TA(0.5) * (r0[1] + r1[0] + r1[2] + r2[1]) + r1[1];
-      st_as<TS, TA>(bc + (size_t)blk * ldc + (size_t)I + (size_t)J * mc, v);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-template <typename TB, typename TS, typename TA, bool VAR>
-__global__ void __launch_bounds__(256) mg_up(const TB* __restrict__ b, const TS* __restrict__ xcoarse,
-                                             TS* __restrict__ x, int m, int mc, size_t ldb, size_t ldc, size_t ldx,
-                                             const TA* __restrict__ st, TA omega, int nu1, int nu2, int tiles_x) {
-  __shared__ TA sb[UWX * UWY], sx0[UWX * UWY], sx1[UWX * UWY], sxc[UCX * UCY];
-  const int tile = blockIdx.x, blk = blockIdx.y;
-  const int X0 = (tile % tiles_x) * UX, Y0 = (tile / tiles_x) * UY;
-  const int H = nu1 + nu2 - 1;
-  const int WX = UX + 2 * H, WY = UY + 2 * H;
-  const int fi0 = X0 - H, fj0 = Y0 - H;
-  const TB* bb = b + (size_t)blk * ldb;
-  for (int t = threadIdx.x; t < WX * WY; t += blockDim.x) {
-    const int li = t % WX, lj = t / WX, i = fi0 + li, j = fj0 + lj;
-    TA v = 0, xv = 0;
-    if (i >= 0 && i < m && j >= 0 && j < m) {
-      v = ld_as<TA>(bb + (size_t)i + (size_t)j * m);
-      const TA* sp = VAR ? st + 9 * ((size_t)i + (size_t)j * m) : nullptr;
-      xv = omega * dinv_at<TA, VAR>(sp) * v;
-    }
-    sb[t] = v;
-    sx0[t] = xv;
-  }
-  // coarse values covering fine [X0 - nu2, X0 + UX + nu2)
-  const int ci0 = ((X0 - nu2) >> 1) - 1, cj0 = ((Y0 - nu2) >> 1) - 1;  // arithmetic shift = floor
-  const int CWX = (UX + 2 * nu2) / 2 + 3, CWY = (UY + 2 * nu2) / 2 + 3;
-  const TS* xcb = xcoarse + (size_t)blk * ldc;
-  for (int t = threadIdx.x; t < CWX * CWY; t += blockDim.x) {
-    const int I = ci0 + t % CWX, J = cj0 + t / CWX;
-    sxc[t] = (I >= 0 && I < mc && J >= 0 && J < mc) ? ld_as<TA>(xcb + (size_t)I + (size_t)J * mc) : TA(0);
-  }
-  __syncthreads();
-  TA* xc = sx0;
-  TA* xn = sx1;
-  for (int s = 2; s <= nu1; ++s) {
-    const int lo = s - 1;
-    for (int t = threadIdx.x; t < WX * WY; t += blockDim.x) {
-      const int li = t % WX, lj = t / WX, i = fi0 + li, j = fj0 + lj;
-      TA v = 0;
-      if (li >= lo && li < WX - lo && lj >= lo && lj < WY - lo && i >= 0 && i < m && j >= 0 && j < m) {
-        const TA* sp = VAR ? st + 9 * ((size_t)i + (size_t)j * m) : nullptr;
-        v = xc[t] + omega * dinv_at<TA, VAR>(sp) * (sb[t] - apply_pt<TA, VAR>(xc, WX, li, lj, sp));
-      }
-      xn[t] = v;
-    }
-    __syncthreads();
-    TA* tmp = xc; xc = xn; xn = tmp;
-  }
-  // coarse-grid correction on fine [X0 - nu2, X0 + UX + nu2)
-  {
-    const int lo = nu1 - 1;
-    for (int t = threadIdx.x; t < WX * WY; t += blockDim.x) {
-      const int li = t % WX, lj = t / WX, i = fi0 + li, j = fj0 + lj;
-      if (li >= lo && li < WX - lo && lj >= lo && lj < WY - lo && i >= 0 && i < m && j >= 0 && j < m) {
-        // fine interior i <-> vertex i+1; even vertex sits on coarse vertex (i+1)/2 (interior (i-1)/2)
-        TA px[2], py[2];
-        int ix[2], iy[2], nx, ny;
-        if (i & 1) { ix[0] = (i - 1) >> 1; px[0] = 1; nx = 1; }
-        else { ix[0] = (i >> 1) - 1; ix[1] = i >> 1; px[0] = px[1] = TA(0.5); nx = 2; }
-        if (j & 1) { iy[0] = (j - 1) >> 1; py[0] = 1; ny = 1; }
-        else { iy[0] = (j >> 1) - 1; iy[1] = j >> 1; py[0] = py[1] = TA(0.5); ny = 2; }
-        TA corr = 0;
-        for (int a = 0; a < ny; ++a)
-          for (int c = 0; c < nx; ++c) corr += py[a] * px[c] * sxc[(iy[a] - cj0) * CWX + (ix[c] - ci0)];
-        xc[t] += corr;
-      }
-    }
-  }
-  __syncthreads();
-  for (int s = 1; s <= nu2; ++s) {
-    const int lo = nu1 - 1 + s;
-    for (int t = threadIdx.x; t < WX * WY; t += blockDim.x) {
-      const int li = t % WX, lj = t / WX, i = fi0 + li, j = fj0 + lj;
-      TA v = 0;
-      if (li >= lo && li < WX - lo && lj >= lo && lj < WY - lo && i >= 0 && i < m && j >= 0 && j < m) {
-        const TA* sp = VAR ? st + 9 * ((size_t)i + (size_t)j * m) : nullptr;
-        v = xc[t] + omega * dinv_at<TA, VAR>(sp) * (sb[t] - apply_pt<TA, VAR>(xc, WX, li, lj, sp));
-      }
-      xn[t] = v;
-    }
-    __syncthreads();
-    TA* tmp = xc; xc = xn; xn = tmp;
-  }
-  TS* xb = x + (size_t)blk * ldx;
-  for (int t = threadIdx.x; t < UX * UY; t += blockDim.x) {
-    const int i = X0 + t % UX, j = Y0 + t / UX;
-    if (i < m && j < m) st_as<TS, TA>(xb + (size_t)i + (size_t)j * m, xc[(j - fj0) * WX + (i - fi0)]);
-  }
-}
 
 // ---------------------------------------------------------------------------
 struct CoarseLevels {
@@ -333,6 +147,14 @@ template <> const float* stencil_ptr<float>(const sg_ctx* h, int l) { return h->
 template <typename TB, typename TS, typename TA>
 int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
+  if (h->const_mean && h->nu1 == 1) {
+    const int tx = (C.m + DCX - 1) / DCX, ty = (C.m + DCY - 1) / DCY;
+    mg_down_c11<TB, TS, TA><<<dim3(tx * ty, nb), 256, 0, h->stream>>>(b, bc, F.m, C.m, F.N, C.N,
+                                                                      (TA)(h->omega * 3.0 / 8.0), tx);
+    SG_CUDA(h, cudaGetLastError());
+    count_launch(h);
+    return SG_OK;
+  }
   const int tiles_x = (C.m + CT - 1) / CT;
   dim3 grid(tiles_x * tiles_x, nb);
   if (h->const_mean)
@@ -348,6 +170,14 @@ int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
 template <typename TB, typename TS, typename TA>
 int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TS* x) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
+  if (h->const_mean && h->nu1 == 1 && h->nu2 == 1) {
+    const int ux = (F.m + UOX - 1) / UOX, uy = (F.m + UOY - 1) / UOY;
+    mg_up_c11<TB, TS, TA><<<dim3(ux * uy, nb), 256, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N,
+                                                                    (TA)(h->omega * 3.0 / 8.0), ux);
+    SG_CUDA(h, cudaGetLastError());
+    count_launch(h);
+    return SG_OK;
+  }
   const int tx = (F.m + UX - 1) / UX, ty = (F.m + UY - 1) / UY;
   dim3 grid(tx * ty, nb);
   if (h->const_mean)
@@ -442,24 +272,27 @@ int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X) {
     return vcycle_t<float, float, float>(h, nb, (const float*)B, (float*)X, W);
   }
   if (bprec == SG_F64) return vcycle_t<double, bf16, float>(h, nb, (const double*)B, (bf16*)X, W);
+  if (bprec == SG_F32) return vcycle_t<float, bf16, float>(h, nb, (const float*)B, (bf16*)X, W);
   return vcycle_t<bf16, bf16, float>(h, nb, (const bf16*)B, (bf16*)X, W);
 }
 
 // B_T^{-1} (Sec. 4.2): degree levels q are dependent stages; the n_q diagonal
 // blocks of one stage are independent and cycled together.
-int precond_blocktri(sg_ctx* h, const double* R, void* Z, int prec, int transpose) {
+int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
+  if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blocktri: FP64 sweep needs FP64 input");
   int rc = ensure_prec_work(h, prec);
   if (rc) return rc;
-  const size_t es = prec_size(prec);
+  const size_t es = prec_size(prec), rs = prec_size(rprec);
+  const int arith = prec == SG_F64 ? SG_F64 : SG_F32;
   for (int s = 0; s <= h->p; ++s) {
     const int q = transpose ? h->p - s : s;
     const int r0 = h->lvl_off[q], nq = h->lvl_off[q + 1] - r0;
     char* Zq = (char*)Z + es * (size_t)r0 * h->Nx;
     if (s == 0) {
-      rc = vcycle_run(h, prec, nq, R + (size_t)r0 * h->Nx, SG_F64, Zq);
+      rc = vcycle_run(h, prec, nq, (const char*)R + rs * (size_t)r0 * h->Nx, rprec, Zq);
     } else {
       // T_q = R_q - sum over the couplings to the previous stage of G_k(i,j) K_k Z_j
-      rc = launch_apply(h, transpose ? 2 : 1, prec, Z, prec, h->work[prec].T, R, r0, nq, r0, 0, prec == SG_F64);
+      rc = launch_apply(h, transpose ? 2 : 1, prec, Z, 0, prec, h->work[prec].T, 0, rprec, R, 0, r0, nq, r0, 0, arith);
       if (rc) return rc;
       rc = vcycle_run(h, prec, nq, h->work[prec].T, prec, Zq);
     }
@@ -469,6 +302,7 @@ int precond_blocktri(sg_ctx* h, const double* R, void* Z, int prec, int transpos
 }
 
 // B_D^{-1} (Sec. 4.1): one V-cycle on every PC block.
-int precond_blockdiag(sg_ctx* h, const double* R, void* Z, int prec) {
-  return vcycle_run(h, prec, h->P, R, SG_F64, Z);
+int precond_blockdiag(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
+  if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blockdiag: FP64 cycle needs FP64 input");
+  return vcycle_run(h, prec, h->P, R, rprec, Z);
 }

@@ -6,7 +6,11 @@
 #include <algorithm>
 #include <vector>
 
+#include "df64.cuh"
 #include "sg_internal.h"
+
+#define SG_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
+  X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
 
 namespace {
 constexpr int NT = SG_NTHREADS_RED;
@@ -34,54 +38,172 @@ __device__ __forceinline__ void reduce_out(double (&acc)[NO], double* partial, d
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (last) {
+    // final sum over the block partials: each warp owns outputs o = warp, warp + 8, ...; its lanes
+    // stride over the blocks in a fixed order and the warp reduces with shuffles (deterministic)
     __threadfence();
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    for (int o = warp; o < nout; o += NT / 32) {
       double v = 0;
-      for (int b = 0; b < (int)gridDim.x; ++b) v += ((volatile double*)partial)[(size_t)b * MAXOUT + o];
-      out[o] = v;
+      for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(partial + (size_t)b * MAXOUT + o);
+      for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+      if (lane == 0) out[o] = v;
     }
     if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
+// h_l = <V_l, w> for l < NV (exact count: no predicated slots) and, in slot NV, <w, w>.
 template <int NV>
-__global__ void __launch_bounds__(NT) k_dots(const double* __restrict__ V, size_t ldv, int nv,
-                                             const double* __restrict__ w, size_t N, int with_ww, double* partial,
-                                             double* out, unsigned* counter) {
+__global__ void __launch_bounds__(NT) k_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ w,
+                                             size_t N, int with_ww, double* partial, double* out, unsigned* counter) {
+  // N: padded length (even; the padding holds zeros); 16-byte loads of two elements
   double acc[NV + 1];
 #pragma unroll
   for (int l = 0; l <= NV; ++l) acc[l] = 0;
-  for (size_t s = blockIdx.x * (size_t)NT + threadIdx.x; s < N; s += (size_t)gridDim.x * NT) {
-    const double wv = w[s];
+  const size_t n2 = N / 2;
+  for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n2; q += (size_t)gridDim.x * NT) {
+    const double2 wv = ((const double2*)w)[q];
 #pragma unroll
-    for (int l = 0; l < NV; ++l)
-      if (l < nv) acc[l] += V[(size_t)l * ldv + s] * wv;
-    acc[NV] += wv * wv;
+    for (int l = 0; l < NV; ++l) {
+      const double2 v = ((const double2*)(V + (size_t)l * ldv))[q];
+      acc[l] = fma(v.x, wv.x, fma(v.y, wv.y, acc[l]));
+    }
+    if (with_ww) acc[NV] = fma(wv.x, wv.x, fma(wv.y, wv.y, acc[NV]));
   }
-  // move the w.w slot next to the last used one
-  double tmp[NV + 1];
+  reduce_out<NV + 1>(acc, partial, out, counter, NV + (with_ww ? 1 : 0));
+}
+
+// w -= sum_l hc_l V_l and ||w||^2
+template <int NV>
+__global__ void __launch_bounds__(NT) k_axpys(const double* __restrict__ V, size_t ldv, const double* __restrict__ hc,
+                                              double* __restrict__ w, size_t N, double* partial, double* out,
+                                              unsigned* counter) {
+  double c[NV];
 #pragma unroll
-  for (int l = 0; l <= NV; ++l) tmp[l] = (l < nv) ? acc[l] : (l == nv ? acc[NV] : 0.0);
-  reduce_out<NV + 1>(tmp, partial, out, counter, nv + (with_ww ? 1 : 0));
+  for (int l = 0; l < NV; ++l) c[l] = hc[l];
+  double acc[1] = {0};
+  const size_t n2 = N / 2;
+  for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n2; q += (size_t)gridDim.x * NT) {
+    double2 v = ((double2*)w)[q];
+#pragma unroll
+    for (int l = 0; l < NV; ++l) {
+      const double2 x = ((const double2*)(V + (size_t)l * ldv))[q];
+      v.x = fma(-c[l], x.x, v.x);
+      v.y = fma(-c[l], x.y, v.y);
+    }
+    ((double2*)w)[q] = v;
+    acc[0] = fma(v.x, v.x, fma(v.y, v.y, acc[0]));
+  }
+  reduce_out<1>(acc, partial, out, counter, 1);
+}
+
+// ---- double-float vectors: hi[0..N), lo[N..2N) ------------------------------
+__device__ __forceinline__ df2 ldf(const float* p, size_t N, size_t i) { return {p[i], p[i + N]}; }
+__device__ __forceinline__ double dacc_to_double(dacc a) { return (double)a.s + (double)a.c; }
+
+template <int NV>
+__global__ void __launch_bounds__(NT) k_dots_df(const float* __restrict__ V, size_t ldv, const float* __restrict__ w,
+                                                size_t N, int with_ww, double* partial, double* out,
+                                                unsigned* counter) {
+  // N: padded length (multiple of 4, lo array at +N, padding zero); 16-byte loads of 4 elements
+  dacc acc[NV + 1];
+#pragma unroll
+  for (int l = 0; l <= NV; ++l) acc[l] = dacc_zero();
+  const size_t n4 = N / 4;
+  for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n4; q += (size_t)gridDim.x * NT) {
+    const float4 wh = ((const float4*)w)[q], wl = ((const float4*)(w + N))[q];
+#pragma unroll
+    for (int l = 0; l < NV; ++l) {
+      const float4 vh = ((const float4*)(V + (size_t)l * ldv))[q];
+      const float4 vl = ((const float4*)(V + (size_t)l * ldv + N))[q];
+      dacc_fma(acc[l], df2{vh.x, vl.x}, df2{wh.x, wl.x});
+      dacc_fma(acc[l], df2{vh.y, vl.y}, df2{wh.y, wl.y});
+      dacc_fma(acc[l], df2{vh.z, vl.z}, df2{wh.z, wl.z});
+      dacc_fma(acc[l], df2{vh.w, vl.w}, df2{wh.w, wl.w});
+    }
+    if (with_ww) {
+      dacc_fma(acc[NV], df2{wh.x, wl.x}, df2{wh.x, wl.x});
+      dacc_fma(acc[NV], df2{wh.y, wl.y}, df2{wh.y, wl.y});
+      dacc_fma(acc[NV], df2{wh.z, wl.z}, df2{wh.z, wl.z});
+      dacc_fma(acc[NV], df2{wh.w, wl.w}, df2{wh.w, wl.w});
+    }
+  }
+  double r[NV + 1];
+#pragma unroll
+  for (int l = 0; l <= NV; ++l) r[l] = dacc_to_double(acc[l]);
+  reduce_out<NV + 1>(r, partial, out, counter, NV + (with_ww ? 1 : 0));
 }
 
 template <int NV>
-__global__ void __launch_bounds__(NT) k_axpys(const double* __restrict__ V, size_t ldv, int nv,
-                                              const double* __restrict__ hc, double* __restrict__ w, size_t N,
-                                              double* partial, double* out, unsigned* counter) {
-  double c[NV];
+__global__ void __launch_bounds__(NT) k_axpys_df(const float* __restrict__ V, size_t ldv, const double* __restrict__ hc,
+                                                 float* __restrict__ w, size_t N, double* partial, double* out,
+                                                 unsigned* counter) {
+  df2 c[NV];
 #pragma unroll
-  for (int l = 0; l < NV; ++l) c[l] = (l < nv) ? hc[l] : 0.0;
-  double acc[1] = {0};
-  for (size_t s = blockIdx.x * (size_t)NT + threadIdx.x; s < N; s += (size_t)gridDim.x * NT) {
-    double v = w[s];
+  for (int l = 0; l < NV; ++l) c[l] = df_from_double(-hc[l]);
+  dacc nn = dacc_zero();
+  const size_t n4 = N / 4;
+  for (size_t q = blockIdx.x * (size_t)NT + threadIdx.x; q < n4; q += (size_t)gridDim.x * NT) {
+    const float4 wh = ((const float4*)w)[q], wl = ((const float4*)(w + N))[q];
+    dacc v0 = {wh.x, wl.x}, v1 = {wh.y, wl.y}, v2 = {wh.z, wl.z}, v3 = {wh.w, wl.w};
+#pragma unroll
+    for (int l = 0; l < NV; ++l) {
+      const float4 xh = ((const float4*)(V + (size_t)l * ldv))[q];
+      const float4 xl = ((const float4*)(V + (size_t)l * ldv + N))[q];
+      dacc_fma(v0, c[l], df2{xh.x, xl.x});
+      dacc_fma(v1, c[l], df2{xh.y, xl.y});
+      dacc_fma(v2, c[l], df2{xh.z, xl.z});
+      dacc_fma(v3, c[l], df2{xh.w, xl.w});
+    }
+    const df2 r0 = dacc_get(v0), r1 = dacc_get(v1), r2 = dacc_get(v2), r3 = dacc_get(v3);
+    ((float4*)w)[q] = make_float4(r0.hi, r1.hi, r2.hi, r3.hi);
+    ((float4*)(w + N))[q] = make_float4(r0.lo, r1.lo, r2.lo, r3.lo);
+    dacc_fma(nn, r0, r0);
+    dacc_fma(nn, r1, r1);
+    dacc_fma(nn, r2, r2);
+    dacc_fma(nn, r3, r3);
+  }
+  double acc[1] = {dacc_to_double(nn)};
+  reduce_out<1>(acc, partial, out, counter, 1);
+}
+
+__global__ void k_scale_df(float* __restrict__ v, size_t N, df2 sc) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const df2 r = df_mul(ldf(v, N, i), sc);
+    v[i] = r.hi;
+    v[i + N] = r.lo;
+  }
+}
+
+template <typename TZ, int NV>
+__global__ void k_update_df(float* __restrict__ U, const TZ* __restrict__ Z, size_t ldz, int nz,
+                            const double* __restrict__ y, size_t N, size_t lo) {
+  df2 c[NV];
+#pragma unroll
+  for (int l = 0; l < NV; ++l) c[l] = (l < nz) ? df_from_double(y[l]) : df2{0.f, 0.f};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    dacc u = dacc_from(ldf(U, lo, i));
 #pragma unroll
     for (int l = 0; l < NV; ++l)
-      if (l < nv) v -= c[l] * V[(size_t)l * ldv + s];
-    w[s] = v;
-    acc[0] += v * v;
+      if (l < nz) dacc_fma(u, c[l], ld_as<float>(Z + (size_t)l * ldz + i));
+    const df2 r = dacc_get(u);
+    U[i] = r.hi;
+    U[i + lo] = r.lo;
   }
-  reduce_out<1>(acc, partial, out, counter, 1);
+}
+
+// split an FP64 vector into a double-float vector; positions [N, lo) of both halves are zeroed
+// (the padding of Krylov vectors must stay zero)
+__global__ void k_df_from_f64(const double* __restrict__ x, float* __restrict__ y, size_t N, size_t lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < lo; i += (size_t)gridDim.x * blockDim.x) {
+    const df2 r = i < N ? df_from_double(x[i]) : df2{0.f, 0.f};
+    y[i] = r.hi;
+    y[i + lo] = r.lo;
+  }
+}
+
+__global__ void k_df_to_f64(const float* __restrict__ x, double* __restrict__ y, size_t N, size_t lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i] + (double)x[i + lo];
 }
 
 __global__ void k_scale(const double* __restrict__ w, double* __restrict__ v, size_t N, double s) {
@@ -202,7 +324,7 @@ int grid_for(size_t N) {
 
 int ensure_reduction(sg_ctx* h) {
   if (h->red_partial) return SG_OK;
-  h->red_blocks = 152 * 4;
+  h->red_blocks = 152 * 8;
   if (cudaMalloc(&h->red_partial, sizeof(double) * MAXOUT * h->red_blocks) != cudaSuccess ||
       cudaMalloc(&h->red_out, sizeof(double) * 4 * MAXOUT) != cudaSuccess ||
       cudaMalloc(&h->red_count, sizeof(unsigned) * 8) != cudaSuccess ||
@@ -224,10 +346,14 @@ int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, si
   if (nv < 0 || nv > 32) return sg_fail(h, SG_E_ARG, "dots: at most 32 vectors per call");
   const int g = red_grid(h, N);
   double* out = h->red_out;
-  if (nv <= 4) k_dots<4><<<g, NT, 0, h->stream>>>(V, ldv, nv, w, N, with_ww, h->red_partial, out, h->red_count);
-  else if (nv <= 8) k_dots<8><<<g, NT, 0, h->stream>>>(V, ldv, nv, w, N, with_ww, h->red_partial, out, h->red_count);
-  else if (nv <= 16) k_dots<16><<<g, NT, 0, h->stream>>>(V, ldv, nv, w, N, with_ww, h->red_partial, out, h->red_count);
-  else k_dots<32><<<g, NT, 0, h->stream>>>(V, ldv, nv, w, N, with_ww, h->red_partial, out, h->red_count);
+  (void)0;
+  switch (nv) {
+    case 0: k_dots<0><<<g, NT, 0, h->stream>>>(V, ldv, w, N, with_ww, h->red_partial, out, h->red_count); break;
+#define SG_C(K) \
+    case K: k_dots<K><<<g, NT, 0, h->stream>>>(V, ldv, w, N, with_ww, h->red_partial, out, h->red_count); break;
+    SG_NV_CASES(SG_C)
+#undef SG_C
+  }
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
   if (out_host) {
@@ -242,14 +368,16 @@ int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, si
 int vec_axpys_norm(sg_ctx* h, const double* V, size_t ldv, int nv, const double* hc, double* w, size_t N, double* nrm2_host) {
   int rc = ensure_reduction(h);
   if (rc) return rc;
-  if (nv < 0 || nv > 32) return sg_fail(h, SG_E_ARG, "axpys: at most 32 vectors per call");
+  if (nv < 1 || nv > 32) return sg_fail(h, SG_E_ARG, "axpys: 1..32 vectors per call");
   const int g = red_grid(h, N);
   double* out = h->red_out + MAXOUT;
   unsigned* cnt = h->red_count + 1;
-  if (nv <= 4) k_axpys<4><<<g, NT, 0, h->stream>>>(V, ldv, nv, hc, w, N, h->red_partial, out, cnt);
-  else if (nv <= 8) k_axpys<8><<<g, NT, 0, h->stream>>>(V, ldv, nv, hc, w, N, h->red_partial, out, cnt);
-  else if (nv <= 16) k_axpys<16><<<g, NT, 0, h->stream>>>(V, ldv, nv, hc, w, N, h->red_partial, out, cnt);
-  else k_axpys<32><<<g, NT, 0, h->stream>>>(V, ldv, nv, hc, w, N, h->red_partial, out, cnt);
+  switch (nv) {
+#define SG_C(K) \
+    case K: k_axpys<K><<<g, NT, 0, h->stream>>>(V, ldv, hc, w, N, h->red_partial, out, cnt); break;
+    SG_NV_CASES(SG_C)
+#undef SG_C
+  }
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
   if (nrm2_host) {
@@ -257,6 +385,87 @@ int vec_axpys_norm(sg_ctx* h, const double* V, size_t ldv, int nv, const double*
     SG_CUDA(h, cudaStreamSynchronize(h->stream));
     *nrm2_host = h->red_host[MAXOUT];
   }
+  return SG_OK;
+}
+
+// double-float versions: V_l hi at V + l*ldv (lo at + N); results in reduction slots 0 / 1
+int df_dots(sg_ctx* h, const float* V, size_t ldv, int nv, const float* w, size_t N, bool with_ww) {
+  int rc = ensure_reduction(h);
+  if (rc) return rc;
+  if (nv < 0 || nv > 32) return sg_fail(h, SG_E_ARG, "dots: at most 32 vectors per call");
+  const int g = red_grid(h, N);
+  double* out = h->red_out;
+  switch (nv) {
+    case 0: k_dots_df<0><<<g, NT, 0, h->stream>>>(V, ldv, w, N, with_ww, h->red_partial, out, h->red_count); break;
+#define SG_C(K) \
+    case K: k_dots_df<K><<<g, NT, 0, h->stream>>>(V, ldv, w, N, with_ww, h->red_partial, out, h->red_count); break;
+    SG_NV_CASES(SG_C)
+#undef SG_C
+  }
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  return SG_OK;
+}
+
+int df_axpys_norm(sg_ctx* h, const float* V, size_t ldv, int nv, const double* hc, float* w, size_t N) {
+  int rc = ensure_reduction(h);
+  if (rc) return rc;
+  if (nv < 1 || nv > 32) return sg_fail(h, SG_E_ARG, "axpys: 1..32 vectors per call");
+  const int g = red_grid(h, N);
+  double* out = h->red_out + MAXOUT;
+  unsigned* cnt = h->red_count + 1;
+  switch (nv) {
+#define SG_C(K) \
+    case K: k_axpys_df<K><<<g, NT, 0, h->stream>>>(V, ldv, hc, w, N, h->red_partial, out, cnt); break;
+    SG_NV_CASES(SG_C)
+#undef SG_C
+  }
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  return SG_OK;
+}
+
+int df_scale(sg_ctx* h, float* v, size_t N, double s) {
+  k_scale_df<<<grid_for(N), 256, 0, h->stream>>>(v, N, df_from_double(s));
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  return SG_OK;
+}
+
+int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t ldz, int nz, const double* y_host,
+              size_t N) {
+  int rc = ensure_reduction(h);
+  if (rc) return rc;
+  const size_t es = prec_size(zprec);
+  for (int c0 = 0; c0 < nz; c0 += 16) {
+    const int cn = std::min(16, nz - c0);
+    double* ydev = h->red_out + 2 * MAXOUT;
+    std::copy(y_host + c0, y_host + c0 + cn, h->red_host + 2 * MAXOUT);
+    SG_CUDA(h, cudaMemcpyAsync(ydev, h->red_host + 2 * MAXOUT, sizeof(double) * cn, cudaMemcpyHostToDevice, h->stream));
+    const void* Zc = (const char*)Z + es * (size_t)c0 * ldz;
+    if (zprec == SG_F32)
+      k_update_df<float, 16><<<grid_for(N), 256, 0, h->stream>>>(U, (const float*)Zc, ldz, cn, ydev, N, lo);
+    else if (zprec == SG_BF16)
+      k_update_df<bf16, 16><<<grid_for(N), 256, 0, h->stream>>>(U, (const bf16*)Zc, ldz, cn, ydev, N, lo);
+    else return sg_fail(h, SG_E_ARG, "df update: Z must be FP32 or BF16");
+    SG_CUDA(h, cudaGetLastError());
+    count_launch(h);
+    SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return SG_OK;
+}
+
+int df_from_f64(sg_ctx* h, const double* x, float* y, size_t N, size_t lo) {
+  k_df_from_f64<<<grid_for(N), 256, 0, h->stream>>>(x, y, N, lo);
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  return SG_OK;
+}
+
+int df_to_f64(sg_ctx* h, const float* x, double* y, size_t N, size_t lo) {
+  k_df_to_f64<<<grid_for(N), 256, 0, h->stream>>>(x, y, N, lo);
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
   return SG_OK;
 }
 

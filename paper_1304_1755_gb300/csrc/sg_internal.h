@@ -32,6 +32,7 @@ struct TermTable {
   int* k = nullptr;
   double* g = nullptr;
   float* gf = nullptr;
+  float* gdf = nullptr;       // g as double-float pairs (hi, lo)
   int nnz = 0;
 };
 
@@ -65,6 +66,7 @@ struct sg_ctx {
   // problem
   int n = 0, m = 0, M = 0, p = 0, P = 0, family = 0;
   size_t Nx = 0, Nc = 0;
+  size_t Np = 0;                        // P * Nx rounded up to a multiple of 64 (Krylov vector stride)
   int nu1 = 1, nu2 = 1;
   double omega = 8.0 / 9.0;
   bool const_mean = true;
@@ -75,6 +77,7 @@ struct sg_ctx {
   // device operator data
   double* coef64 = nullptr;             // (M+1) * Nc
   float* coef32 = nullptr;
+  float* coefdf = nullptr;              // (M+1) * Nc double-float pairs (hi, lo)
   TermTable t_all, t_lower, t_upper, t_off;   // all / lower / upper / off-diagonal couplings
   double* pvec = nullptr;               // P doubles of device scratch (objective)
   // multigrid hierarchy
@@ -154,14 +157,17 @@ void galerkin_stencils(int n0, int nlev, const double* abar_cells, std::vector<s
 // which: 0 = all terms (Y = A X), 1 = lower terms, 2 = upper terms, 3 = off-diagonal terms.
 // Computes Y_i (i in [row0, row0 + nrows)) = epi ? R_i - S_i : S_i,
 // S_i = sum over the table's terms; Y rows are offset by ybase, R rows by rbase.
-int launch_apply(sg_ctx* h, int which, int xprec, const void* X, int yprec, void* Y,
-                 const double* R, int row0, int nrows, int ybase, int rbase, int arith64);
+// Precisions: SG_F64 / SG_F32 / SG_BF16 plain arrays, SG_DF64 hi array with the lo
+// array at offset *lo (elements).  arith: SG_F64, SG_F32 or SG_DF64.
+int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int yprec, void* Y, size_t ylo,
+                 int rprec, const void* R, size_t rlo, int row0, int nrows, int ybase, int rbase, int arith);
 
 // k_mg.cu
 int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X);
 int ensure_prec_work(sg_ctx* h, int prec);
-int precond_blocktri(sg_ctx* h, const double* R, void* Z, int prec, int transpose);
-int precond_blockdiag(sg_ctx* h, const double* R, void* Z, int prec);
+// R is FP64 (rprec SG_F64) or FP32 (rprec SG_F32, e.g. the hi array of a double-float vector)
+int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose);
+int precond_blockdiag(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
 
 // k_vec.cu
 int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host);
@@ -176,6 +182,16 @@ int vec_dot_pairs(sg_ctx* h, int npairs, const double* const* xs, const void* co
 int vec_axpy_prec(sg_ctx* h, double a, int xprec, const void* x, double* y, size_t N);  // y += a x
 int ensure_reduction(sg_ctx* h);
 int copy_red(sg_ctx* h, int slot, int count, double* out_host);
+// Double-float Krylov vectors: hi[0..Np), lo[Np..2Np) with the padded length Np (a multiple
+// of 64, padding kept at zero); dots/axpys/scale take Np, the others the true length N
+// and the lo offset.
+int df_dots(sg_ctx* h, const float* V, size_t ldv, int nv, const float* w, size_t Np, bool with_ww);   // red slot 0
+int df_axpys_norm(sg_ctx* h, const float* V, size_t ldv, int nv, const double* hc_dev, float* w, size_t Np);  // slot 1
+int df_scale(sg_ctx* h, float* v, size_t Np, double s);
+int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t ldz, int nz, const double* y_host,
+              size_t N);
+int df_from_f64(sg_ctx* h, const double* x, float* y, size_t N, size_t lo);
+int df_to_f64(sg_ctx* h, const float* x, double* y, size_t N, size_t lo);
 // adjoint helpers
 int adj_cell_forms(sg_ctx* h, const double* U, const double* L, double* g_abar);
 int objective_dots(sg_ctx* h, const double* U, double* mu_host);

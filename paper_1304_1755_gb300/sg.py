@@ -12,7 +12,8 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsg.so")
 
-F64, F32, BF16 = 0, 1, 2
+F64, F32, BF16, DF64 = 0, 1, 2, 3
+ARITH_F64, ARITH_DF64 = 0, 1
 LEGENDRE, HERMITE = 0, 1
 GMRES, FGMRES, GPCG, PCG = 0, 1, 2, 3
 PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG = 0, 1, 2
@@ -36,7 +37,8 @@ class Problem(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("precond", ctypes.c_int), ("restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("pc_prec", ctypes.c_int),
-                ("transpose", ctypes.c_int), ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int)]
+                ("transpose", ctypes.c_int), ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int),
+                ("arith", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -167,8 +169,8 @@ class Handle:
         _check(lib().sg_vcycle(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)
 
     def solve(self, F, U, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8, pc_prec=F64,
-              transpose=False, x0_given=False, reorth=1, check=True):
-        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), int(x0_given), reorth)
+              transpose=False, x0_given=False, reorth=0, arith=ARITH_F64, check=True):
+        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), int(x0_given), reorth, arith)
         info = SolveInfo()
         rc = lib().sg_solve(self.h, _ptr(F), _ptr(U), ctypes.byref(o), ctypes.byref(info))
         if check and rc not in (0,):

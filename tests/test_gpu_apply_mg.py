@@ -66,6 +66,29 @@ def test_apply_low_precision(shape, prec):
     assert np.all(np.abs(host(Y) - ref) <= bound)
 
 
+def _to_df(x):
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    return np.concatenate([hi, lo]), hi.astype(np.float64) + lo.astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[0]}M{s[1]}p{s[2]}f{s[3]}{s[4]}")
+def test_apply_double_float(shape):
+    """Double-float operator (FP32 pairs): the input is the df split of an FP64 vector; the result
+    hi + lo must match the FP64 oracle to 2e-13 (|A| |X|) (the df significand is 48 bits)."""
+    import torch
+    n, M, p, fam, mean = shape
+    pr = Pair(n, M, p, fam, mean=mean)
+    xdf, X = _to_df(inputs.uniform(14, pr.N))
+    ref = osg.apply(pr.sys, X)
+    Y = torch.empty(2 * pr.N, dtype=torch.float32, device="cuda")
+    pr.h.apply(dev(xdf), Y, 3)
+    torch.cuda.synchronize()
+    y = Y.cpu().numpy().astype(np.float64)
+    got = y[:pr.N] + y[pr.N:]
+    assert np.all(np.abs(got - ref) <= 2e-13 * _abs_apply(pr.sys, X) + 1e-300)
+
+
 def test_residual_fp64():
     import torch
     pr = Pair(33, 2, 2)

@@ -76,7 +76,7 @@ def test_c1_iteration_counts_bt_below_bd():
     assert abs(it_o - its[sg.PC_BLOCKTRI]) <= 1
 
 
-@pytest.mark.parametrize("n,M,p,fam,mean", [(65, 3, 3, basis.HERMITE, "lognormal"), (129, 4, 2, basis.LEGENDRE, "one"),
+@pytest.mark.parametrize("n,M,p,fam,mean", [(65, 3, 3, basis.HERMITE, "lognormal"), (129, 2, 2, basis.LEGENDRE, "one"),
                                               (17, 1, 0, basis.LEGENDRE, "one"), (5, 6, 4, basis.LEGENDRE, "one")])
 def test_solves_other_shapes(n, M, p, fam, mean):
     import torch
@@ -89,6 +89,39 @@ def test_solves_other_shapes(n, M, p, fam, mean):
         assert info.status == 0
         err = np.linalg.norm(host(U) - Ustar) / np.linalg.norm(Ustar)
         assert err <= (1e-8 if pcp == sg.F64 else 1e-6)
+
+
+@pytest.mark.parametrize("n,M,p,fam,mean,pcp", [(33, 2, 2, basis.LEGENDRE, "one", sg.F32),
+                                                 (33, 2, 2, basis.LEGENDRE, "one", sg.BF16),
+                                                 (65, 3, 3, basis.HERMITE, "lognormal", sg.BF16),
+                                                 (129, 2, 2, basis.LEGENDRE, "one", sg.F32)])
+def test_double_float_fgmres_matches_direct(n, M, p, fam, mean, pcp):
+    """Double-float Arnoldi basis and operator (SG_ARITH_DF64): same bar as FP64 runs."""
+    import torch
+    pr = Pair(n, M, p, fam, sigma=0.3, mean=mean)
+    F = osg.rhs(pr.sys, inputs.rhs_nodes(3, n))
+    Ustar = _direct(pr, F)
+    U = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
+    info = pr.h.solve(dev(F), U, pc_prec=pcp, tol=1e-10, restart=30, arith=sg.ARITH_DF64)
+    assert info.status == 0 and info.relres_true <= 1e-10
+    err = np.linalg.norm(host(U) - Ustar) / np.linalg.norm(Ustar)
+    assert err <= 1e-8, err
+
+
+def test_repeated_solves_reuse_workspace_deterministically():
+    """Workspace is reused across calls and modes (its padding must stay zero): a double-float
+    solve, a strict FP64 GPCG solve that scribbles on the shared work vectors, then the
+    double-float solve again must give bit-identical results."""
+    import torch
+    pr = Pair(33, 2, 3, sigma=0.3)
+    F = dev(osg.rhs(pr.sys, inputs.rhs_nodes(4, 33)))
+    U1 = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
+    U2, U3 = torch.zeros_like(U1), torch.zeros_like(U1)
+    pr.h.solve(F, U1, pc_prec=sg.BF16, arith=sg.ARITH_DF64, tol=1e-10)
+    pr.h.solve(F, U2, method=sg.GPCG, tol=1e-10)
+    pr.h.solve(F, U3, pc_prec=sg.BF16, arith=sg.ARITH_DF64, tol=1e-10)
+    assert torch.equal(U1, U3)
+    assert float((U1 - U2).abs().max()) <= 1e-8 * float(U2.abs().max())
 
 
 def test_transpose_solve_and_host_buffers():
