@@ -63,8 +63,11 @@ typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2, SG_DF64 = 3 } sg_prec;
  * preconditioner must then be SG_F32 or SG_BF16). */
 typedef enum { SG_ARITH_F64 = 0, SG_ARITH_DF64 = 1 } sg_arith;
 typedef enum { SG_LEGENDRE = 0, SG_HERMITE = 1 } sg_family;
-typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3 } sg_method;
-typedef enum { SG_PC_NONE = 0, SG_PC_BLOCKTRI = 1, SG_PC_BLOCKDIAG = 2 } sg_pc;
+/* SG_BGS: the stationary block Gauss-Seidel iteration U += B_T^{-1}(F - A U) (Sec. 4.2). */
+typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3, SG_BGS = 4 } sg_method;
+/* SG_PC_BLOCKSYM: B_S = B_T diag(A)^{-1} B_T^T, the symmetric block Gauss-Seidel
+ * preconditioner of Sec. 4.2 (lower sweep, the exact diagonal blocks K_0, upper sweep). */
+typedef enum { SG_PC_NONE = 0, SG_PC_BLOCKTRI = 1, SG_PC_BLOCKDIAG = 2, SG_PC_BLOCKSYM = 3 } sg_pc;
 
 /* One SG problem (Sec. 2-3).  coef is a HOST array of (M+1) rows of (n-1)^2
  * per-cell values, cell e = cx + cy (n-1): row 0 is the mean coefficient
@@ -161,6 +164,9 @@ int sg_residual(sg_handle h, const double* F, const double* U, double* R);
 int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose);
 /* Z = B_D^{-1} R (Sec. 4.1): one V-cycle on every PC block. */
 int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec);
+/* Z = B_S^{-1} R (Sec. 4.2): lower sweep, multiplication by the diagonal blocks K_0
+ * (exact), upper sweep; symmetric positive definite, for PCG.  R FP64, Z in prec. */
+int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec);
 /* One V(nu1,nu2) cycle on K_0 from a zero guess for nblocks stacked blocks of
  * N_x values: B FP64 (device), X in prec (device). */
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec);

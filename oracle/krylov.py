@@ -124,3 +124,18 @@ def pcg(apply_A, apply_M, b, x0=None, tol=1e-8, maxit=1000):
         rz = rz_new
     rt = b - apply_A(x)
     return x, its, np.linalg.norm(rt) / bnorm
+
+
+def block_gauss_seidel(apply_A, apply_BT, b, x0=None, tol=1e-8, maxit=1000):
+    """Stationary block Gauss-Seidel iteration of Sec. 4.2 (the B-GS rows of Table 3):
+    x_{k+1} = x_k + B_T^{-1} (b - A x_k), zero initial guess."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    r = b - apply_A(x)
+    its = 0
+    while np.linalg.norm(r) > tol * bnorm and its < maxit:
+        x = x + apply_BT(r)
+        r = b - apply_A(x)
+        its += 1
+    return x, its, np.linalg.norm(r) / bnorm

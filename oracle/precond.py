@@ -68,3 +68,12 @@ def block_tri_inv(sys, solver, R, transpose=False):
                 T -= c
         Z[i] = solver(T)
     return Z.reshape(-1)
+
+
+def block_sym_inv(sys, solver, R):
+    """Z = B_S^{-1} R for the symmetric block Gauss-Seidel preconditioner of Sec. 4.2,
+    B_S = B_T diag(A)^{-1} B_T^T with diag(A) = I (x) K_0:  a lower sweep, the exact
+    diagonal blocks K_0, then an upper sweep."""
+    Z1 = block_tri_inv(sys, solver, R).reshape(sys.P, sys.Nx)
+    Z2 = (sys.K[0] @ Z1.T).T
+    return block_tri_inv(sys, solver, np.ascontiguousarray(Z2).reshape(-1), transpose=True)

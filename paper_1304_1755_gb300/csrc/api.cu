@@ -36,6 +36,15 @@ int upload_terms(sg_ctx* h, TermTable& T, int which) {
     const df2 d = df_from_double(v);
     tgd.push_back(d.hi), tgd.push_back(d.lo);
   }
+  // weight slot of each term: 0 for the mean term, 1 + (k-1) p + n for c_k gamma(n), n = min(alpha_k, beta_k)
+  std::vector<int> tw(tj.size(), 0);
+  for (int i = 0; i + 1 < (int)rp.size(); ++i)
+    for (int t = rp[i]; t < rp[i + 1]; ++t) {
+      const int k = tk[t];
+      if (k == 0) continue;
+      const int ai = h->alpha[(size_t)i * h->M + k - 1], aj = h->alpha[(size_t)tj[t] * h->M + k - 1];
+      tw[t] = 1 + (k - 1) * h->p + std::min(ai, aj);
+    }
   int rc;
   if ((rc = upload(h, &T.row_ptr, rp.data(), rp.size()))) return rc;
   if ((rc = upload(h, &T.j, tj.data(), tj.size()))) return rc;
@@ -43,11 +52,33 @@ int upload_terms(sg_ctx* h, TermTable& T, int which) {
   if ((rc = upload(h, &T.g, tg.data(), tg.size()))) return rc;
   if ((rc = upload(h, &T.gf, tgf.data(), tgf.size()))) return rc;
   if ((rc = upload(h, &T.gdf, tgd.data(), tgd.size()))) return rc;
+  if ((rc = upload(h, &T.ws, tw.data(), tw.size()))) return rc;
   return SG_OK;
 }
 
+// Double-float weight table W[slot][e] = c_k(e) gamma(n) (slot 0: c_0), when it fits in 2 GB.
+int upload_weights(sg_ctx* h) {
+  const size_t slots = 1 + (size_t)h->M * h->p;
+  if (slots * h->Nc * 8 > (size_t)2 << 30) return SG_OK;
+  std::vector<float> w(2 * slots * h->Nc);
+  for (size_t e = 0; e < h->Nc; ++e) {
+    const df2 d = df_from_double(h->coef_h[e]);
+    w[2 * e] = d.hi, w[2 * e + 1] = d.lo;
+  }
+  for (int k = 1; k <= h->M; ++k)
+    for (int nn = 0; nn < h->p; ++nn) {
+      const size_t s = 1 + (size_t)(k - 1) * h->p + nn;
+      const double gm = gamma_1d(h->family, nn);
+      for (size_t e = 0; e < h->Nc; ++e) {
+        const df2 d = df_from_double(h->coef_h[(size_t)k * h->Nc + e] * gm);
+        w[2 * (s * h->Nc + e)] = d.hi, w[2 * (s * h->Nc + e) + 1] = d.lo;
+      }
+    }
+  return upload(h, &h->wdf, w.data(), w.size());
+}
+
 void free_terms(TermTable& T) {
-  cudaFree(T.row_ptr), cudaFree(T.j), cudaFree(T.k), cudaFree(T.g), cudaFree(T.gf), cudaFree(T.gdf);
+  cudaFree(T.row_ptr), cudaFree(T.j), cudaFree(T.k), cudaFree(T.g), cudaFree(T.gf), cudaFree(T.gdf), cudaFree(T.ws);
   T = TermTable{};
 }
 
@@ -77,6 +108,7 @@ double host_dot(sg_ctx* h, const double* x, const double* y, size_t N, int* rc) 
 int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec, int transpose) {
   if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, rprec, R, Z, prec, transpose);
   if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, rprec, R, Z, prec);
+  if (pc == SG_PC_BLOCKSYM) return precond_blocksym(h, rprec, R, Z, prec);
   return vec_cast(h, rprec, R, prec, Z, h->Nx * (size_t)h->P);
 }
 
@@ -187,7 +219,12 @@ struct OpsDF {
       SG_CUDA(h, cudaMemcpyAsync(v(0), Fd, sizeof(float) * 2 * Np, cudaMemcpyDeviceToDevice, h->stream));
       return SG_OK;
     }
-    return launch_apply(h, 0, SG_DF64, Ud, Np, SG_DF64, v(0), Np, SG_DF64, Fd, Np, 0, h->P, 0, 0, SG_DF64);
+    // restart (and final check): the true residual of the FP64 iterate in IEEE FP64, then split
+    int rc;
+    double* r64 = h->ktmp + 2 * Np;
+    if ((rc = df_to_f64(h, Ud, U, N, Np))) return rc;
+    if ((rc = apply_f64(h, 0, SG_F64, U, SG_F64, r64, F))) return rc;
+    return df_from_f64(h, r64, v(0), N, Np);
   }
   int norm2(int l, double* out) {
     int rc;
@@ -224,15 +261,19 @@ int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& in
   bool u_zero = !o.x0_given;
   for (;;) {
     {
-      PhaseScope ps(h, 0);
-      if ((rc = ops.residual(u_zero))) return rc;   // v_0 = F - A U
+      PhaseScope ps(h, 3);
+      if ((rc = ops.residual(u_zero))) return rc;   // v_0 = F - A U, the IEEE FP64 true residual
     }
     double b2 = 0;
     if ((rc = ops.norm2(0, &b2))) return rc;
     const double beta = std::sqrt(b2);
     if (!std::isfinite(beta)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
     info.relres_true = beta / bnorm;
-    if (beta <= o.tol * bnorm) { info.relres_est = info.relres_true; break; }
+    if (beta <= o.tol * bnorm) {
+      info.relres_est = info.relres_true;
+      h->true_res_valid = true;    // the caller need not recompute it
+      break;
+    }
     if (its >= o.maxit) { info.iters = its; ops.finish(); return SG_E_NOCONV; }
     if ((rc = ops.scale(0, 1.0 / beta))) return rc;
     std::fill(g.begin(), g.end(), 0.0);
@@ -378,6 +419,37 @@ int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg
 }
 
 // Standard PCG (Sec. 4.2, with B_D or the SPD B_S); B_T is accepted but not SPD.
+// Stationary block Gauss-Seidel (Sec. 4.2, the B-GS rows of Table 3): U += B^{-1}(F - A U).
+int solve_bgs(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
+  const size_t N = h->Nx * (size_t)h->P;
+  const int zp = o.pc_prec;
+  int rc = ensure_krylov(h, 1, 1, zp);
+  if (rc) return rc;
+  double* r = h->ktmp;
+  const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
+  if (rc) return rc;
+  if (!std::isfinite(bnorm)) return sg_fail(h, SG_E_NONFINITE, "non-finite right-hand side");
+  if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  int its = 0;
+  for (;;) {
+    if ((rc = apply_f64(h, 0, SG_F64, U, SG_F64, r, F))) return rc;
+    const double rr = host_dot(h, r, r, N, &rc);
+    if (rc) return rc;
+    if (!std::isfinite(rr)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
+    info.relres_true = info.relres_est = std::sqrt(rr) / bnorm;
+    if (std::sqrt(rr) <= o.tol * bnorm) { h->true_res_valid = true; break; }
+    if (its >= o.maxit) { info.iters = its; return SG_E_NOCONV; }
+    {
+      PhaseScope ps(h, 1);
+      if ((rc = apply_precond(h, o.precond, SG_F64, r, h->kz, zp, o.transpose))) return rc;
+    }
+    if ((rc = vec_axpy_prec(h, 1.0, zp, h->kz, U, N))) return rc;
+    ++its;
+  }
+  info.iters = its;
+  return SG_OK;
+}
+
 int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
   const size_t N = h->Nx * (size_t)h->P;
   const int zp = o.pc_prec;
@@ -423,11 +495,13 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
 
 void destroy_ctx(sg_ctx* h) {
   if (!h) return;
-  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->pvec);
-  free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->pvec);
+  free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off), free_terms(h->t_diag);
   for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
   for (auto& W : h->work) {
-    cudaFree(W.T);
+    cudaFree(W.T), cudaFree(W.S1), cudaFree(W.S2);
     for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(W.b[l]), cudaFree(W.x[l]);
   }
   cudaFree(h->red_partial), cudaFree(h->red_out), cudaFree(h->red_count), cudaFreeHost(h->red_host);
@@ -501,7 +575,7 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
       (rc = upload(h, &h->coef32, c32.data(), c32.size())) || (rc = upload(h, &h->coefdf, cdf.data(), cdf.size())) ||
       (rc = upload_terms(h, h->t_all, 0)) ||
       (rc = upload_terms(h, h->t_lower, 1)) || (rc = upload_terms(h, h->t_upper, 2)) ||
-      (rc = upload_terms(h, h->t_off, 3))) {
+      (rc = upload_terms(h, h->t_off, 3)) || (rc = upload_terms(h, h->t_diag, 4)) || (rc = upload_weights(h))) {
     std::string e = h->err;
     destroy_ctx(h);
     return sg_fail(nullptr, rc, "sg_setup: " + e);
@@ -584,6 +658,11 @@ int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec) {
   return precond_blockdiag(h, SG_F64, R, Z, prec);
 }
 
+int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec) {
+  if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocksym: bad argument") : SG_E_ARG;
+  return precond_blocksym(h, SG_F64, R, Z, prec);
+}
+
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
   if (!h || !B || !X || prec < 0 || prec > 2 || nblocks < 0 || nblocks > h->P)
     return h ? sg_fail(h, SG_E_ARG, "sg_vcycle: bad argument") : SG_E_ARG;
@@ -593,7 +672,7 @@ int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
 int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info_out) {
   if (!h || !F || !U || !opts) return h ? sg_fail(h, SG_E_ARG, "sg_solve: null argument") : SG_E_ARG;
   sg_solve_opts o = *opts;
-  if (o.method < SG_GMRES || o.method > SG_PCG || o.precond < 0 || o.precond > 2 || o.pc_prec < 0 || o.pc_prec > 2 ||
+  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 3 || o.pc_prec < 0 || o.pc_prec > 2 ||
       !(o.tol > 0) || o.maxit < 0)
     return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
   if ((o.method == SG_GMRES || o.method == SG_FGMRES) && (o.restart < 1 || o.restart > 32))
@@ -620,10 +699,12 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
   SG_CUDA(h, cudaEventRecord(e0, h->stream));
   if (!o.x0_given) SG_CUDA(h, cudaMemsetAsync(dU, 0, sizeof(double) * N, h->stream));
   int rc;
+  h->true_res_valid = false;
   if (o.method == SG_GMRES || o.method == SG_FGMRES) rc = solve_gmres(h, dF, dU, o, info, o.method == SG_FGMRES);
   else if (o.method == SG_GPCG) rc = solve_gpcg(h, dF, dU, o, info);
-  else rc = solve_pcg(h, dF, dU, o, info);
-  if (rc == SG_OK || rc == SG_E_NOCONV) {
+  else if (o.method == SG_PCG) rc = solve_pcg(h, dF, dU, o, info);
+  else rc = solve_bgs(h, dF, dU, o, info);
+  if ((rc == SG_OK && !h->true_res_valid) || rc == SG_E_NOCONV) {
     // true residual in FP64
     int rc2 = ensure_krylov(h, 1, 1, o.pc_prec);
     if (!rc2) rc2 = apply_f64(h,0, SG_F64, dU, SG_F64, h->ktmp, dF);

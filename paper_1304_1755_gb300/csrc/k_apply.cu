@@ -29,6 +29,7 @@ namespace {
 constexpr int CXN = 32, CYN = 8, NT = CXN * CYN;   // cells per CTA
 constexpr int OXN = CXN - 1, OYN = CYN - 1;        // output nodes per CTA
 constexpr int ROWS = 4;
+constexpr int MAXT = 16;                            // staged coupling terms per row (more: read from global)
 
 struct ApplyArgs {
   const void* X;
@@ -40,6 +41,8 @@ struct ApplyArgs {
   const double* c64;
   const float* c32;
   const df2* cdf;
+  const df2* wdf;      // optional table of weights c_k(e) gamma_n as double-float, slot-major
+  const int* ws;       // weight slot of each term
   const int* row_ptr;
   const int* tj;
   const int* tk;
@@ -101,6 +104,7 @@ template <> struct Load<DFS> {
   }
 
 struct ArF32 {
+  static constexpr bool kUsesTable = false;
   typedef float T;
   typedef float Acc;
   static __device__ __forceinline__ T weight(const ApplyArgs& a, int k, size_t e, int t) {
@@ -121,6 +125,7 @@ struct ArF32 {
 };
 
 struct ArF64 {
+  static constexpr bool kUsesTable = false;
   typedef double T;
   typedef double Acc;
   static __device__ __forceinline__ T weight(const ApplyArgs& a, int k, size_t e, int t) {
@@ -143,7 +148,10 @@ struct ArF64 {
 struct ArDF {
   typedef df2 T;
   typedef dacc Acc;
+  // with the weight table, k is the term's weight slot (precomputed c_k(e) gamma products)
+  static constexpr bool kUsesTable = true;
   static __device__ __forceinline__ T weight(const ApplyArgs& a, int k, size_t e, int t) {
+    if (a.wdf) return a.wdf[(size_t)k * a.Nc + e];
     return df_mul(a.cdf[(size_t)k * a.Nc + e], a.gdf[t]);
   }
   static __device__ __forceinline__ Acc zero() { return dacc_zero(); }
@@ -287,14 +295,29 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   const int rbeg = a.row0 + group * ROWS;
   const int rend = min(rbeg + ROWS, a.row0 + a.nrows);
   const int ox = tid % OXN, oy = tid / OXN;
+  // stage the coupling terms of this CTA's rows in shared memory (one round trip instead of
+  // one per term): column j and mode k
+  __shared__ int s_tj[ROWS * MAXT], s_tk[ROWS * MAXT];
+  const int tall0 = a.row_ptr[rbeg], tall1 = a.row_ptr[rend];
+  const bool staged = tall1 - tall0 <= ROWS * MAXT;
+  if (staged) {
+    for (int t = tall0 + tid; t < tall1; t += NT) {
+      s_tj[t - tall0] = a.tj[t];
+      s_tk[t - tall0] = (AR::kUsesTable && a.wdf) ? a.ws[t] : a.tk[t];
+    }
+    __syncthreads();
+  }
   for (int i = rbeg; i < rend; ++i) {
     const int t0 = a.row_ptr[i], t1 = a.row_ptr[i + 1];
     typename AR::State st;
     AR::init(st);
     if (cell_ok) {
+#pragma unroll 2
       for (int t = t0; t < t1; ++t) {
-        const size_t base = (size_t)a.tj[t] * a.Nx;
-        const T w = AR::weight(a, a.tk[t], e, t);
+        const int jj = staged ? s_tj[t - tall0] : a.tj[t];
+        const int kk = staged ? s_tk[t - tall0] : ((AR::kUsesTable && a.wdf) ? a.ws[t] : a.tk[t]);
+        const size_t base = (size_t)jj * a.Nx;
+        const T w = AR::weight(a, kk, e, t);
         const typename LX::Z za = ina ? LX::at(a.X, a.xlo, base + ia) : LX::zero();
         const typename LX::Z zb = inb ? LX::at(a.X, a.xlo, base + ia + 1) : LX::zero();
         const typename LX::Z zc = inc ? LX::at(a.X, a.xlo, base + ia + 1 + m) : LX::zero();
@@ -384,10 +407,15 @@ int pick_x(sg_ctx* h, ApplyArgs& a, int xprec, int yprec, int rprec) {
 int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int yprec, void* Y, size_t ylo,
                  int rprec, const void* R, size_t rlo, int row0, int nrows, int ybase, int rbase, int arith) {
   if (nrows <= 0) return SG_OK;
-  const TermTable& T = which == 0 ? h->t_all : (which == 1 ? h->t_lower : (which == 2 ? h->t_upper : h->t_off));
+  const TermTable& T = which == 0   ? h->t_all
+                       : which == 1 ? h->t_lower
+                       : which == 2 ? h->t_upper
+                       : which == 3 ? h->t_off
+                                    : h->t_diag;
   ApplyArgs a{};
   a.X = X, a.xlo = xlo, a.Y = Y, a.ylo = ylo, a.R = R, a.rlo = rlo;
   a.c64 = h->coef64, a.c32 = h->coef32, a.cdf = (const df2*)h->coefdf;
+  a.wdf = (const df2*)h->wdf, a.ws = T.ws;
   a.row_ptr = T.row_ptr, a.tj = T.j, a.tk = T.k, a.g64 = T.g, a.g32 = T.gf, a.gdf = (const df2*)T.gdf;
   a.row0 = row0, a.nrows = nrows, a.ybase = ybase, a.rbase = rbase, a.n = h->n, a.m = h->m;
   a.Nx = h->Nx, a.Nc = h->Nc;

@@ -20,6 +20,7 @@
 
 #include "sg_internal.h"
 #include "mg_kernels.cuh"
+#include "mg_c11.cuh"
 
 namespace {
 constexpr int NC0 = 33;                                  // levels with n <= NC0 run in mg_coarse
@@ -148,9 +149,13 @@ template <typename TB, typename TS, typename TA>
 int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1) {
-    const int tx = (C.m + DCX - 1) / DCX, ty = (C.m + DCY - 1) / DCY;
-    mg_down_c11<TB, TS, TA><<<dim3(tx * ty, nb), 256, 0, h->stream>>>(b, bc, F.m, C.m, F.N, C.N,
-                                                                      (TA)(h->omega * 3.0 / 8.0), tx);
+    // strip height: as tall as possible while still giving every SM ~24 warps
+    int srows = SLIDE_ROWS;
+    const int sx = (C.m + 31) / 32;
+    while (srows > 2 && (long)sx * ((C.m + srows - 1) / srows) * nb < 152L * 24) srows /= 2;
+    const int ns = sx * ((C.m + srows - 1) / srows);
+    mg_down_slide<TB, TS, TA><<<dim3((ns + SLIDE_WARPS - 1) / SLIDE_WARPS, nb), 32 * SLIDE_WARPS, 0, h->stream>>>(
+        b, bc, F.m, C.m, F.N, C.N, (TA)(h->omega * 3.0 / 8.0), sx, ns, srows);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;
@@ -171,9 +176,12 @@ template <typename TB, typename TS, typename TA>
 int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TS* x) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1 && h->nu2 == 1) {
-    const int ux = (F.m + UOX - 1) / UOX, uy = (F.m + UOY - 1) / UOY;
-    mg_up_c11<TB, TS, TA><<<dim3(ux * uy, nb), 256, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N,
-                                                                    (TA)(h->omega * 3.0 / 8.0), ux);
+    int srows = SLIDE_ROWS;
+    const int sx = (F.m + 63) / 64;
+    while (srows > 2 && (long)sx * ((F.m + 2 * srows - 1) / (2 * srows)) * nb < 152L * 24) srows /= 2;
+    const int ns = sx * ((F.m + 2 * srows - 1) / (2 * srows));
+    mg_up_slide<TB, TS, TA><<<dim3((ns + SLIDE_WARPS - 1) / SLIDE_WARPS, nb), 32 * SLIDE_WARPS, 0, h->stream>>>(
+        b, xc, x, F.m, C.m, F.N, C.N, F.N, (TA)(h->omega * 3.0 / 8.0), sx, ns, srows);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;
@@ -276,12 +284,51 @@ int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X) {
   return vcycle_t<bf16, bf16, float>(h, nb, (const bf16*)B, (bf16*)X, W);
 }
 
-// B_T^{-1} (Sec. 4.2): degree levels q are dependent stages; the n_q diagonal
-// blocks of one stage are independent and cycled together.
-int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
-  if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blocktri: FP64 sweep needs FP64 input");
+// A preconditioner application is a fixed sequence of about ten launches per degree
+// stage (many on tiny coarse grids), so on a non-default stream it is captured once
+// per operand set into a CUDA graph and replayed; the cache key is (R, Z, rprec,
+// prec, kind).  Nested capture by the caller falls back to direct launches.
+template <class Body>
+int run_graphed(sg_ctx* h, const void* R, const void* Z, int rprec, int prec, int kind, Body&& body) {
   int rc = ensure_prec_work(h, prec);
   if (rc) return rc;
+  if (h->stream == nullptr) return body();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SG_CUDA(h, cudaStreamIsCapturing(h->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return body();
+  const auto key = std::make_tuple(R, Z, rprec, prec, kind);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (h->graphs.size() >= 512) {
+      for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+      h->graphs.clear();
+    }
+    const long long before = h->tr.launches[h->phase];
+    SG_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    rc = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ec != cudaSuccess) return sg_fail(h, SG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return sg_fail(h, SG_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    it = h->graphs.emplace(key, sg_ctx::GraphEntry{ex, h->tr.launches[h->phase] - before}).first;
+  } else {
+    count_launch(h, (int)it->second.kernels);
+  }
+  SG_CUDA(h, cudaGraphLaunch(it->second.exec, h->stream));
+  return SG_OK;
+}
+
+// B_T^{-1} (Sec. 4.2): degree levels q are dependent stages; the n_q diagonal
+// blocks of one stage are independent and cycled together.
+static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
+  int rc;
   const size_t es = prec_size(prec), rs = prec_size(rprec);
   const int arith = prec == SG_F64 ? SG_F64 : SG_F32;
   for (int s = 0; s <= h->p; ++s) {
@@ -301,8 +348,31 @@ int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int
   return SG_OK;
 }
 
+int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
+  if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blocktri: FP64 sweep needs FP64 input");
+  return run_graphed(h, R, Z, rprec, prec, transpose ? 2 : 1,
+                     [&] { return precond_blocktri_direct(h, rprec, R, Z, prec, transpose); });
+}
+
+// B_S^{-1} (Sec. 4.2): B_S = B_T diag(A)^{-1} B_T^T, applied as a lower sweep, the exact
+// diagonal blocks K_0 (one stencil pass) and an upper sweep.
+int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
+  if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blocksym: FP64 sweep needs FP64 input");
+  PrecWork& W = h->work[prec];
+  const size_t N = h->Nx * (size_t)h->P;
+  const int sprec = prec == SG_F64 ? SG_F64 : SG_F32;
+  if (!W.S1) {
+    if (cudaMalloc(&W.S1, prec_size(prec) * N) != cudaSuccess || cudaMalloc(&W.S2, prec_size(sprec) * N) != cudaSuccess)
+      return sg_fail(h, SG_E_ALLOC, "alloc symmetric sweep buffers");
+  }
+  int rc;
+  if ((rc = precond_blocktri(h, rprec, R, W.S1, prec, 0))) return rc;
+  if ((rc = launch_apply(h, 4, prec, W.S1, 0, sprec, W.S2, 0, SG_F64, nullptr, 0, 0, h->P, 0, 0, sprec))) return rc;
+  return precond_blocktri(h, sprec, W.S2, Z, prec, 1);
+}
+
 // B_D^{-1} (Sec. 4.1): one V-cycle on every PC block.
 int precond_blockdiag(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
   if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blockdiag: FP64 cycle needs FP64 input");
-  return vcycle_run(h, prec, h->P, R, rprec, Z);
+  return run_graphed(h, R, Z, rprec, prec, 0, [&] { return vcycle_run(h, prec, h->P, R, rprec, Z); });
 }

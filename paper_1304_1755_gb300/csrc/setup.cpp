@@ -136,8 +136,9 @@ void build_terms(const sg_ctx* h, int which, std::vector<int>& row_ptr, std::vec
   tj.clear(), tk.clear(), tg.clear();
   for (int i = 0; i < P; ++i) {
     std::vector<int> a(h->alpha.begin() + (size_t)i * M, h->alpha.begin() + (size_t)(i + 1) * M);
-    if (which == 0) { tj.push_back(i); tk.push_back(0); tg.push_back(1.0); }
-    for (int k = 0; k < M; ++k) {
+    // which: 0 all, 1 lower, 2 upper, 3 off-diagonal, 4 the mean (diagonal) term only
+    if (which == 0 || which == 4) { tj.push_back(i); tk.push_back(0); tg.push_back(1.0); }
+    for (int k = 0; k < M && which != 4; ++k) {
       if (which != 2 && a[k] > 0) {   // lower neighbour i - e_k
         std::vector<int> b = a;
         b[k] -= 1;

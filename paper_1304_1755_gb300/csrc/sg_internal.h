@@ -5,7 +5,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "sg.h"
@@ -33,6 +35,7 @@ struct TermTable {
   double* g = nullptr;
   float* gf = nullptr;
   float* gdf = nullptr;       // g as double-float pairs (hi, lo)
+  int* ws = nullptr;          // weight slot: 0 for the mean term, 1 + (k-1) p + n for c_k gamma(n)
   int nnz = 0;
 };
 
@@ -50,6 +53,8 @@ struct PrecWork {
   void* T = nullptr;                    // stage right-hand side, n_q_max * N_x
   void* b[SG_MAX_LEVELS] = {};          // level >= 1 right-hand sides, P * N_l
   void* x[SG_MAX_LEVELS] = {};          // level >= 1 solutions, P * N_l
+  void* S1 = nullptr;                   // symmetric sweep: lower-sweep result (P * N_x)
+  void* S2 = nullptr;                   //                  K_0 times it, FP32 (FP64 for an FP64 sweep)
 };
 
 // Per-phase event tracing (sg_timing_*).  Phase 0 outer operator, 1 preconditioner,
@@ -78,7 +83,8 @@ struct sg_ctx {
   double* coef64 = nullptr;             // (M+1) * Nc
   float* coef32 = nullptr;
   float* coefdf = nullptr;              // (M+1) * Nc double-float pairs (hi, lo)
-  TermTable t_all, t_lower, t_upper, t_off;   // all / lower / upper / off-diagonal couplings
+  float* wdf = nullptr;                 // (1 + M p) * Nc double-float weights c_k(e) gamma(n) (or null)
+  TermTable t_all, t_lower, t_upper, t_off, t_diag;   // all / lower / upper / off-diagonal / mean term
   double* pvec = nullptr;               // P doubles of device scratch (objective)
   // multigrid hierarchy
   int nlev = 0;
@@ -99,6 +105,13 @@ struct sg_ctx {
   double* dstage = nullptr;             // staging for host F/U (2 vectors)
   Tracer tr;
   int phase = 3;
+  bool true_res_valid = false;          // the solver already computed the final FP64 true residual
+  // CUDA graphs of whole preconditioner applications, keyed by their operands
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::map<std::tuple<const void*, const void*, int, int, int>, GraphEntry> graphs;
   std::string err;
 };
 
@@ -154,7 +167,8 @@ void build_terms(const sg_ctx* h, int which, std::vector<int>& row_ptr, std::vec
 void galerkin_stencils(int n0, int nlev, const double* abar_cells, std::vector<std::vector<double>>& st);
 
 // k_apply.cu
-// which: 0 = all terms (Y = A X), 1 = lower terms, 2 = upper terms, 3 = off-diagonal terms.
+// which: 0 = all terms (Y = A X), 1 = lower terms, 2 = upper terms, 3 = off-diagonal terms,
+// 4 = the mean term only (Y = (I (x) K_0) X).
 // Computes Y_i (i in [row0, row0 + nrows)) = epi ? R_i - S_i : S_i,
 // S_i = sum over the table's terms; Y rows are offset by ybase, R rows by rbase.
 // Precisions: SG_F64 / SG_F32 / SG_BF16 plain arrays, SG_DF64 hi array with the lo
@@ -168,6 +182,7 @@ int ensure_prec_work(sg_ctx* h, int prec);
 // R is FP64 (rprec SG_F64) or FP32 (rprec SG_F32, e.g. the hi array of a double-float vector)
 int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose);
 int precond_blockdiag(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
+int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
 
 // k_vec.cu
 int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host);

@@ -15,8 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libsg.so")
 F64, F32, BF16, DF64 = 0, 1, 2, 3
 ARITH_F64, ARITH_DF64 = 0, 1
 LEGENDRE, HERMITE = 0, 1
-GMRES, FGMRES, GPCG, PCG = 0, 1, 2, 3
-PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG = 0, 1, 2
+GMRES, FGMRES, GPCG, PCG, BGS = 0, 1, 2, 3, 4
+PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM = 0, 1, 2, 3
 
 STATUS = {0: "SG_OK", -1: "SG_E_ARG", -2: "SG_E_ALLOC", -3: "SG_E_CUDA", -4: "SG_E_NOCONV",
           -5: "SG_E_BREAKDOWN", -6: "SG_E_NONFINITE", -7: "SG_E_TIMEOUT", -8: "SG_E_STATE"}
@@ -65,6 +65,7 @@ SIGNATURES = {
     "sg_residual": (ctypes.c_int, [VP, VP, VP, VP]),
     "sg_precond_blocktri": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_precond_blockdiag": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
+    "sg_precond_blocksym": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
     "sg_vcycle": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_solve": (ctypes.c_int, [VP, VP, VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "sg_objective": (ctypes.c_int, [VP, VP, DP, VP]),
@@ -164,6 +165,9 @@ class Handle:
 
     def precond_blockdiag(self, R, Z, prec=F64):
         _check(lib().sg_precond_blockdiag(self.h, _ptr(R), _ptr(Z), prec), self.h)
+
+    def precond_blocksym(self, R, Z, prec=F64):
+        _check(lib().sg_precond_blocksym(self.h, _ptr(R), _ptr(Z), prec), self.h)
 
     def vcycle(self, B, X, nblocks, prec=F64):
         _check(lib().sg_vcycle(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)

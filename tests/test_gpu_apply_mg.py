@@ -127,12 +127,43 @@ def test_vcycle(n, mean, nu, prec):
         assert np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("prec", [0, 2], ids=["f64", "bf16"])
+def test_preconditioner_graph_replay_matches_direct(prec):
+    """On a non-default stream each preconditioner application is captured once as a CUDA graph
+    and replayed; results must be bit-identical to direct launches on the default stream."""
+    import torch
+    from paper_1304_1755_gb300 import sg
+    pr = Pair(129, 3, 3, basis.LEGENDRE)
+    R = dev(inputs.uniform(41, pr.N))
+    dt = torch.float64 if prec == 0 else torch.bfloat16
+    Z0 = torch.empty(pr.N, dtype=dt, device="cuda")
+    pr.h.precond_blocktri(R, Z0, prec)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        h2 = sg.Handle(129, 3, 3, basis.LEGENDRE, pr.coef, stream=s)
+        Z = torch.empty(pr.N, dtype=dt, device="cuda")
+        for _ in range(3):                      # first call captures, the others replay
+            Z.zero_()
+            h2.precond_blocktri(R, Z, prec)
+            s.synchronize()
+            assert torch.equal(Z, Z0)
+        Zd = torch.empty(pr.N, dtype=dt, device="cuda")
+        h2.precond_blockdiag(R, Zd, prec)
+    s.synchronize()
+    Zd0 = torch.empty(pr.N, dtype=dt, device="cuda")
+    pr.h.precond_blockdiag(R, Zd0, prec)
+    torch.cuda.synchronize()
+    assert torch.equal(Zd, Zd0)
+    h2.close()
+
+
 PC_SHAPES = [(9, 2, 3, basis.LEGENDRE, "one"), (33, 2, 2, basis.LEGENDRE, "one"),
              (65, 3, 2, basis.HERMITE, "lognormal"), (129, 2, 3, basis.LEGENDRE, "one")]
 
 
 @pytest.mark.parametrize("shape", PC_SHAPES, ids=lambda s: f"n{s[0]}M{s[1]}p{s[2]}{s[4]}")
-@pytest.mark.parametrize("kind", ["tri", "tri_T", "diag"])
+@pytest.mark.parametrize("kind", ["tri", "tri_T", "diag", "sym"])
 @pytest.mark.parametrize("prec", [0, 1, 2], ids=["f64", "f32", "bf16"])
 def test_preconditioners(shape, kind, prec):
     import torch
@@ -142,12 +173,16 @@ def test_preconditioners(shape, kind, prec):
     solver = pr.oracle_vsolver()
     if kind == "diag":
         ref = precond.block_diag_inv(pr.sys, solver, R)
+    elif kind == "sym":
+        ref = precond.block_sym_inv(pr.sys, solver, R)
     else:
         ref = precond.block_tri_inv(pr.sys, solver, R, transpose=(kind == "tri_T"))
     dt = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[prec]
     Z = torch.empty(pr.N, dtype=dt, device="cuda")
     if kind == "diag":
         pr.h.precond_blockdiag(dev(R), Z, prec)
+    elif kind == "sym":
+        pr.h.precond_blocksym(dev(R), Z, prec)
     else:
         pr.h.precond_blocktri(dev(R), Z, prec, transpose=(kind == "tri_T"))
     torch.cuda.synchronize()

@@ -37,6 +37,9 @@ CASES = [  # method, precond, pc_prec, restart
     (sg.FGMRES, sg.PC_BLOCKTRI, sg.F32, 30),
     (sg.FGMRES, sg.PC_BLOCKTRI, sg.BF16, 30),
     (sg.FGMRES, sg.PC_NONE, sg.F64, 30),
+    (sg.PCG, sg.PC_BLOCKSYM, sg.F64, 0),
+    (sg.FGMRES, sg.PC_BLOCKSYM, sg.F32, 30),
+    (sg.BGS, sg.PC_BLOCKTRI, sg.F64, 0),
 ]
 
 

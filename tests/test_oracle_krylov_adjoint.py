@@ -77,3 +77,17 @@ def test_adjoint_gradient_matches_central_differences():
         assert abs(fd - g_abar @ d) < 1e-7 * abs(fd) + 1e-14
     fd = (J_of(abar, sigma + eps) - J_of(abar, sigma - eps)) / (2 * eps)
     assert abs(fd - g_sigma) < 1e-7 * abs(fd)
+
+
+def test_block_gauss_seidel_and_bs_pcg_match_direct():
+    s, A, F, solver = _c1()
+    Ud = sg.solve_direct(A, F)
+    Av = lambda v: A @ v
+    U, its, rr = krylov.block_gauss_seidel(Av, lambda r: precond.block_tri_inv(s, solver, r), F, tol=1e-12)
+    assert rr <= 1e-12 and np.linalg.norm(U - Ud) / np.linalg.norm(Ud) < 1e-9
+    # one step from zero is exactly the block-triangular preconditioner applied to F
+    U1, _, _ = krylov.block_gauss_seidel(Av, lambda r: precond.block_tri_inv(s, solver, r), F, maxit=1)
+    assert np.allclose(U1, precond.block_tri_inv(s, solver, F), atol=1e-15)
+    U, its2, rr = krylov.pcg(Av, lambda r: precond.block_sym_inv(s, solver, r), F, tol=1e-12)
+    assert rr <= 1e-12 and np.linalg.norm(U - Ud) / np.linalg.norm(Ud) < 1e-9
+    assert its2 < its

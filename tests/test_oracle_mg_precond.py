@@ -150,3 +150,18 @@ def test_ideal_schur_minimal_polynomial_degree_two():
     Bt = np.block([[Ah, np.zeros_like(W.T)], [W, S]])
     E = np.linalg.solve(Bt, A) - np.eye(A.shape[0])
     assert np.abs(E @ E).max() < 1e-12 * np.abs(E).max() + 1e-13
+
+
+def test_block_sym_is_dense_bs_and_spd():
+    """B_S = B_T diag(A)^{-1} B_T^T (Sec. 4.2) with exact blocks: forward/diag/backward
+    substitution equals the dense solve, and B_S is symmetric positive definite."""
+    s = _system(n=5, M=2, p=2, sigma=0.4)
+    A = sg.assemble(s).toarray()
+    BT = _lower_block_triangular(A, s.P, s.Nx)
+    D = np.kron(np.eye(s.P), s.K[0].toarray())
+    BS = BT @ np.linalg.solve(D, BT.T)
+    assert np.abs(BS - BS.T).max() < 1e-12 * np.abs(BS).max()
+    assert np.linalg.eigvalsh(0.5 * (BS + BS.T)).min() > 0
+    R = np.random.default_rng(5).standard_normal(s.P * s.Nx)
+    solver = precond.DiagSolver(s.K[0])
+    assert np.allclose(precond.block_sym_inv(s, solver, R), np.linalg.solve(BS, R), atol=1e-12)
