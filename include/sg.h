@@ -170,6 +170,24 @@ int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec);
 /* One V(nu1,nu2) cycle on K_0 from a zero guess for nblocks stacked blocks of
  * N_x values: B FP64 (device), X in prec (device). */
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec);
+/* sg_vcycle without any device allocation (the paper has no counterpart: this is a
+ * library-usage variant of the V-cycle of Sec. 4.1).  Same arguments and result as
+ * sg_vcycle, but the coarse-level buffers come from one fixed 32 MiB array compiled
+ * into the library instead of the handle's workspace, which sg_vcycle allocates on
+ * its first call.  It is meant for callers that must not allocate: code running
+ * under a caching allocator that already holds the device's free memory, or inside
+ * latency-bound loops where cudaMalloc's implicit device synchronisation is not
+ * acceptable.  Needs 2 * sum_{l=1..lc} round_up(s * nblocks * N_l, 256) bytes (s =
+ * bytes per value of prec, N_l the interior nodes of level l, lc the last level
+ * handled by the level kernels; 0 for n <= 33); a request above 32 MiB returns
+ * SG_E_ARG with the required size in sg_last_error and launches nothing.  The first
+ * call on each device (made with that device current) looks up the array's device
+ * address; make that first call before capturing a stream into a CUDA graph.  All
+ * calls in the process share the one array per device and it keeps the last call's
+ * contents (nothing in it needs clearing: a call writes every value before reading
+ * it), so calls that overlap in time, from any handle or stream, race and give
+ * wrong results: serialise them. */
+int sg_vcycle_static(sg_handle h, const double* B, void* X, int nblocks, int prec);
 
 /* Solve A U = F (or A^T U = F).  F, U: FP64, host or device pointers (host
  * buffers are staged through device memory inside the call).  info may be

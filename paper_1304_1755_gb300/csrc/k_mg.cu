@@ -17,6 +17,8 @@
 // Arithmetic type TA is double for SG_F64 and float otherwise; storage TS is
 // double, float or bf16 (bf16: FP32 accumulation, storage only).
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "sg_internal.h"
 #include "mg_kernels.cuh"
@@ -375,4 +377,76 @@ int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
 int precond_blockdiag(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
   if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blockdiag: FP64 cycle needs FP64 input");
   return run_graphed(h, R, Z, rprec, prec, 0, [&] { return vcycle_run(h, prec, h->P, R, rprec, Z); });
+}
+
+// ---------------------------------------------------------------------------
+// sg_vcycle_static: the V-cycle of sg_vcycle with its coarse-level buffers taken from
+// a fixed array compiled into the library instead of the handle's lazily allocated
+// workspace, so a call never allocates device memory.
+//
+// Layout inside the array: for l = 1 .. lc (the levels below the fine grid that the
+// level kernels touch), the right-hand sides b_l then the solutions x_l, each nblocks x
+// N_l values of the cycle's storage type, every region starting on a 256-byte boundary.
+// Levels coarser than lc live in the single-CTA kernel's shared memory and need no storage.
+// Every value a call reads from the array was written earlier in the same call (the
+// restriction writes all of b_{l+1}, the coarse kernel all of x_lc, the prolongation
+// all of x_l), so nothing has to be cleared between calls.
+namespace {
+constexpr size_t VCYCLE_SCRATCH_BYTES = size_t(32) << 20;   // 32 MiB
+__device__ __align__(256) unsigned char g_vcycle_scratch[VCYCLE_SCRATCH_BYTES];
+
+constexpr int SCRATCH_MAX_DEVICES = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[SCRATCH_MAX_DEVICES] = {};
+
+// Looks up (once per device, with that device current) the device address of the array.
+int scratch_address(sg_ctx* h, unsigned char** out) {
+  int dev = 0;
+  SG_CUDA(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= SCRATCH_MAX_DEVICES) return sg_fail(h, SG_E_ARG, "sg_vcycle_static: device index out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vcycle_scratch);
+    if (e != cudaSuccess || !p)
+      return sg_fail(h, SG_E_CUDA, std::string("sg_vcycle_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_scratch_addr[dev];
+  return SG_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t static_scratch_bytes(const sg_ctx* h, int nblocks, int prec) {
+  size_t need = 0;
+  for (int l = 1; l <= h->lc; ++l) need += 2 * align256(prec_size(prec) * (size_t)nblocks * h->lev[l].N);
+  return need;
+}
+}  // namespace
+
+extern "C" int sg_vcycle_static(sg_handle h, const double* B, void* X, int nblocks, int prec) {
+  if (!h || !B || !X || prec < 0 || prec > 2 || nblocks < 0 || nblocks > h->P)
+    return h ? sg_fail(h, SG_E_ARG, "sg_vcycle_static: bad argument") : SG_E_ARG;
+  if (nblocks == 0) return SG_OK;
+  const size_t need = static_scratch_bytes(h, nblocks, prec);
+  if (need > VCYCLE_SCRATCH_BYTES)
+    return sg_fail(h, SG_E_ARG, "sg_vcycle_static: " + std::to_string(nblocks) + " blocks need " +
+                                    std::to_string(need) + " bytes of scratch, the static array holds " +
+                                    std::to_string(VCYCLE_SCRATCH_BYTES) + "; use sg_vcycle or fewer blocks");
+  unsigned char* base = nullptr;
+  int rc = scratch_address(h, &base);
+  if (rc) return rc;
+  PrecWork W;                                     // views into the array; nothing is allocated
+  size_t off = 0;
+  for (int l = 1; l <= h->lc; ++l) {
+    const size_t bytes = align256(prec_size(prec) * (size_t)nblocks * h->lev[l].N);
+    W.b[l] = base + off;
+    off += bytes;
+    W.x[l] = base + off;
+    off += bytes;
+  }
+  if (prec == SG_F64) return vcycle_t<double, double, double>(h, nblocks, B, (double*)X, W);
+  if (prec == SG_F32) return vcycle_t<double, float, float>(h, nblocks, B, (float*)X, W);
+  return vcycle_t<double, bf16, float>(h, nblocks, B, (bf16*)X, W);
 }

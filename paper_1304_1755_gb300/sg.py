@@ -67,6 +67,7 @@ SIGNATURES = {
     "sg_precond_blockdiag": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
     "sg_precond_blocksym": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
     "sg_vcycle": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
+    "sg_vcycle_static": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_solve": (ctypes.c_int, [VP, VP, VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "sg_objective": (ctypes.c_int, [VP, VP, DP, VP]),
     "sg_adjoint_gradients": (ctypes.c_int, [VP, VP, VP, ctypes.c_double, VP, DP]),
@@ -171,6 +172,11 @@ class Handle:
 
     def vcycle(self, B, X, nblocks, prec=F64):
         _check(lib().sg_vcycle(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)
+
+    def vcycle_static(self, B, X, nblocks, prec=F64):
+        """sg_vcycle_static: the same cycle with no device allocation (coarse levels in a
+        fixed 32 MiB array shared by every caller in the process; calls must not overlap)."""
+        _check(lib().sg_vcycle_static(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)
 
     def solve(self, F, U, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8, pc_prec=F64,
               transpose=False, x0_given=False, reorth=0, arith=ARITH_F64, check=True):
