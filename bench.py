@@ -18,6 +18,7 @@ bounded sample of the same workload instead (see ``CpuSample``).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,9 +36,21 @@ WORKLOADS = {
                name="sg_c2_257sq_M4_legendre_p4_P70_sigma0.3_fgmres30_fp32pc"),
     "c1": dict(n=33, M=2, p=2, family=0, sigma=0.3, restart=30, pc_prec=0, tol=1e-8, f_seed=None,
                name="sg_c1_33sq_M2_legendre_p2_P6_gmres30_fp64"),
+    # the c3 chaos space on a 513 x 513 grid with FGMRES(4): every kernel of the c3 solve on
+    # vectors of 439 MB (> L2) with about 5 GB on the device, for detailed kernel profiles
+    "c3s": dict(n=513, M=6, p=4, family=1, sigma=0.2, restart=4, pc_prec=2, tol=1e-8, f_seed=None,
+                name="sg_c3_copy_513sq_M6_hermite_p4_P210_fgmres4_bf16pc"),
+    # adjoint gradient of J = E[int u] + Var[int u] / 2 w.r.t. the per-cell mean and sigma
+    "c4": dict(n=257, M=4, p=3, family=0, sigma=0.4, restart=30, pc_prec=1, tol=1e-8, abar_seed=2,
+               name="sg_c4_adjoint_257sq_M4_legendre_p3_P35_sigma0.4_lognormal_mean"),
+    # 64 uneven systems (grid 65^2..513^2, M 2..6, p 2..4, sigma U[0.1, 0.5], Legendre, f = 1):
+    # FGMRES(30) + block-triangular preconditioner in FP32, FP64 outer loop
+    "c5": dict(count=64, batch_seed=5, family=0, restart=30, pc_prec=1, tol=1e-8, nstreams=16,
+               name="sg_c5_batch64_uneven_65to513sq_M2to6_p2to4_legendre_fgmres30_fp32pc"),
 }
 PREC_NAME = {0: "f64", 1: "f32", 2: "bf16"}
 METRIC = "time to rel. residual 1e-8 (block-tri GMRES+MG) and SG-apply HBM GB/s"
+C5_METRIC = "aggregate unknowns solved per second (64 uneven SG systems, block-tri FGMRES+MG to 1e-8)"
 
 
 def _peaks():
@@ -104,13 +117,33 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(values):
+    """Element-wise maximum over the ranks of the process group (the slowest replica decides a
+    replica run's time); the values unchanged without one.  NCCL groups reduce on the GPU, gloo
+    groups on the CPU."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def build_problem(wl):
     import numpy as np
     from paper_1304_1755_gb300 import inputs, sg
     coef, _ = sg.sg_kl_coef(wl["n"], wl["M"], wl["sigma"])
     n = wl["n"]
     Nx = (n - 2) ** 2
-    P = __import__("math").comb(wl["M"] + wl["p"], wl["p"])
+    P = math.comb(wl["M"] + wl["p"], wl["p"])
     f = np.ones(Nx) if wl["f_seed"] is None else inputs.rhs_nodes(wl["f_seed"], n)
     F = np.zeros(P * Nx)
     F[:Nx] = f / (n - 1) ** 2           # F = e_0 (x) h^2 f  (lumped load vector)
@@ -119,9 +152,27 @@ def build_problem(wl):
 
 def k1_bytes(wl, xprec_bytes, yprec_bytes):
     n = wl["n"]
-    P = __import__("math").comb(wl["M"] + wl["p"], wl["p"])
+    P = math.comb(wl["M"] + wl["p"], wl["p"])
     Nx, Nc = (n - 2) ** 2, (n - 1) ** 2
     return (xprec_bytes + yprec_bytes) * Nx * P + 8 * (wl["M"] + 1) * Nc
+
+
+def terms_per_row(wl):
+    """Couplings per output row of A = sum_k G_k (x) K_k: the mean term plus r = 2 x lower pairs / P."""
+    M, p = wl["M"], wl["p"]
+    P = math.comb(M + p, p)
+    return (P + 2 * M * math.comb(M + p - 1, p - 1)) / P
+
+
+def k1_flops(wl, df):
+    """Algorithmic flops of one outer-operator launch.  FP64: N (8 (1 + r) + r + 16) (corner mixing,
+    per-cell weights, element matrix and accumulation).  Double-float: the FP32 flops (add, multiply
+    = 1, fused multiply-add = 2) of the exact feature-domain scheme, 83 per coupling (exact features
+    38, three compensated products 45) plus 116 per unknown (features 32, node sums 84)."""
+    n = wl["n"]
+    N = (n - 2) ** 2 * math.comb(wl["M"] + wl["p"], wl["p"])
+    t = terms_per_row(wl)
+    return N * (83 * t + 116) if df else N * (8 * t + (t - 1) + 16)
 
 
 def run_ours(args, wl, rank, world):
@@ -147,9 +198,8 @@ def run_ours(args, wl, rank, world):
                 pc_prec=wl["pc_prec"], reorth=0, arith=arith)
     for _ in range(args.warmup):
         h.solve(F, U, **opts)
-    if world > 1:
-        torch.distributed.barrier()
     torch.cuda.synchronize()
+    barrier()
     infos = []
     h.timing_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -159,15 +209,12 @@ def run_ours(args, wl, rank, world):
             infos.append(h.solve(F, U, **opts))
         e1.record(stream)
         torch.cuda.synchronize()
+    barrier()
     ms_total = e0.elapsed_time(e1)
     phase_ms, phase_launches = h.timing_read()
     h.timing_enable(False)
     clocks = clk.summary()
-    t_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t)
+    t_step = max_over_ranks([ms_total / args.steps])[0]
     # parity at full size: independent residual check of the last solution on sampled rows is in
     # tests/; here record the library's own recomputed FP64 residual
     its = [i.iters for i in infos]
@@ -191,6 +238,27 @@ def run_ours(args, wl, rank, world):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
+    # the same solve in plain FP64 (FP64 preconditioner, FP64 Krylov arithmetic) on the same GPU
+    vs64 = None
+    if not args.no_fp64_compare and (wl["pc_prec"] != sg.F64 or arith != sg.ARITH_F64):
+        opts64 = dict(opts, pc_prec=sg.F64, arith=sg.ARITH_F64)
+        U64 = torch.zeros_like(U)
+        h.solve(F, U64, **opts64)
+        torch.cuda.synchronize()
+        n64 = max(1, min(args.steps, 2))
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(n64):
+            info64 = h.solve(F, U64, **opts64)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        t64 = e2.elapsed_time(e3) / n64
+        h.solve(F, U, **opts)
+        torch.cuda.synchronize()
+        vs64 = {"ms_per_step": round(t64, 3), "iterations": info64.iters, "relres_true": info64.relres_true,
+                "speedup_of_mixed": round(t64 / t_step, 3),
+                "solution_rel_diff": float(torch.linalg.norm(U - U64) / torch.linalg.norm(U64))}
+        del U64
     launches_total = sum(phase_launches)
     out = {
         "metric": METRIC,
@@ -210,7 +278,8 @@ def run_ours(args, wl, rank, world):
                    "unknowns": N, "restart": wl["restart"], "tol": wl["tol"],
                    "krylov_arith": "df64" if arith == sg.ARITH_DF64 else "f64",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (1.76 GB per vector)" if wl["n"] >= 1025 else "L2-resident vectors"},
+                   "l2": (f"inputs larger than L2 ({8 * N / 1e9:.2f} GB per vector), no flush" if 8 * N > 129e6 else
+                          "vectors fit in L2 (no flush: small-case timing)")},
         "iterations": its[-1],
         "relres_true": relres,
         "sg_apply_gbs": round(k1_gbs, 1),
@@ -219,23 +288,288 @@ def run_ours(args, wl, rank, world):
         "gpu_launches": int(launches_total),
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "clocks": clocks,
+        "vs_plain_fp64": vs64,
     }
-    # dominant kernel: the phase with the largest device time
+    # roofline of the dominant kernel, the outer operator (k_apply): it is bound by arithmetic
+    # (double-float: FP32 pipe; strict mode: FP64 units), not by HBM, on GB300
     names = ["operator", "preconditioner", "gram_schmidt", "other"]
     dom = max(range(4), key=lambda i: phase_ms[i])
+    df = arith == sg.ARITH_DF64
+    fl = k1_flops(wl, df)
+    achieved = fl / (k1_launch_ms * 1e-3) / 1e12
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if df else 1.25
     out["roofline"] = {
-        "kernel": "k_apply (outer SG operator, FP64 arithmetic)",
+        "kernel": "k_apply<ArDF, bf16, DFS> (outer SG operator, double-float)" if df else
+                  "k_apply<ArF64> (outer SG operator, FP64)",
         "dominant_phase": names[dom],
-        "bound": "hbm",
-        "achieved": round(k1_gbs, 1),
-        "peak": hbm,
-        "unit": "GB/s",
-        "frac": round(k1_gbs / hbm, 4),
+        "bound": "alu",
+        "achieved": round(achieved, 2),
+        "peak": round(peak, 2),
+        "unit": "TFLOP/s",
+        "frac": round(achieved / peak, 4),
         "traffic": None,
-        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+        "launch_ms": round(k1_launch_ms, 4),
+        "flops_per_launch": fl,
+        "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock (FP32 flops of the "
+                        "double-float scheme)") if df else "nominal FP64 1.25 TFLOP/s (profiling recipe)",
+        "hbm_gbs": round(k1_gbs, 1),
+        "hbm_frac_of_measured": round(k1_gbs / hbm, 4),
     }
     h.close()
     return out
+
+
+def run_c4(args, wl, rank, world):
+    """Time per adjoint gradient: forward block-triangular FGMRES solve, J and dJ/dU, the transpose
+    solve (upper sweep) and the gradient kernels, all on the GPU through the C ABI; against the
+    plain FP64 forward solve alone."""
+    import numpy as np
+    import torch
+    from paper_1304_1755_gb300 import build as B
+    from paper_1304_1755_gb300 import inputs, sg
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if not os.path.exists(sg.LIB_PATH):
+        B.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n, M, p = wl["n"], wl["M"], wl["p"]
+    unit, _ = sg.sg_kl_coef(n, M, 1.0)
+    coef = unit.copy()
+    coef[0] = inputs.lognormal_cells(wl["abar_seed"], n, 0.2)
+    coef[1:] *= wl["sigma"]
+    h = sg.Handle(n, M, p, wl["family"], coef, stream=stream)
+    N = h.P * h.Nx
+    F = torch.zeros(N, dtype=torch.float64, device="cuda")
+    F[:h.Nx] = 1.0 / (n - 1) ** 2
+    U, G, Lam = torch.zeros_like(F), torch.empty_like(F), torch.zeros_like(F)
+    g_abar = torch.empty((n - 1) ** 2, dtype=torch.float64, device="cuda")
+    opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=wl["restart"], maxit=400, tol=wl["tol"],
+                pc_prec=wl["pc_prec"], reorth=0, arith=sg.ARITH_DF64)
+
+    def gradient():
+        fi = h.solve(F, U, **opts)
+        J = h.objective(U, G)
+        ai = h.solve(G, Lam, transpose=True, **opts)
+        gs = h.adjoint_gradients(U, Lam, wl["sigma"], g_abar)
+        return fi, ai, J, gs
+
+    for _ in range(args.warmup):
+        gradient()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.timing_enable(True)
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            fi, ai, J, gs = gradient()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    t_step = max_over_ranks([e0.elapsed_time(e1) / args.steps])[0]
+    clocks = clk.summary()
+    _, c4_launches = h.timing_read()
+    h.timing_enable(False)
+    opts64 = dict(opts, pc_prec=sg.F64, arith=sg.ARITH_F64)
+    U64 = torch.zeros_like(F)
+    h.solve(F, U64, **opts64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        i64 = h.solve(F, U64, **opts64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / args.steps
+    # end to end: host right-hand side in, gradient out
+    Fh = F.cpu().pin_memory()
+    gh = torch.empty((n - 1) ** 2, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.solve(Fh.numpy(), U, **opts)
+    h.objective(U, G)
+    h.solve(G, Lam, transpose=True, **opts)
+    h.adjoint_gradients(U, Lam, wl["sigma"], g_abar)
+    gh.copy_(g_abar)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    out = {
+        "metric": "time per adjoint gradient dJ/d(abar, sigma) (forward + transpose block-tri FGMRES+MG to 1e-8)",
+        "value": round(t_step / 1e3, 6), "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_step, 3), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 storage, double-float Krylov arithmetic, preconditioner f32",
+        "data": "synthetic (lognormal mean coefficient seed 2, KL modes, f = 1)",
+        "config": {"workload": wl["name"], "unknowns": N, "parameters": (n - 1) ** 2 + 1,
+                   "l2": "vectors fit in L2 (no flush: small-case timing)"},
+        "J": J, "dJ_dsigma": gs, "grad_abar_norm": float(torch.linalg.norm(g_abar)),
+        "iterations": {"forward": fi.iters, "adjoint": ai.iters},
+        "vs_plain_fp64_forward_solve": {"ms_per_step": round(t64, 3), "iterations": i64.iters,
+                                        "gradient_over_fp64_solve": round(t_step / t64, 3)},
+        "gpu_launches": int(sum(c4_launches)),
+        "e2e": {"value": round(t_e2e, 6), "unit": "s", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 8 * (n - 1) ** 2},
+        "clocks": clocks, "roofline": None,
+    }
+    h.close()
+    return out
+
+
+def c5_systems(wl):
+    """The uneven batch: per system (n, M, p, sigma) from the seeded recipe; sigma is lowered where
+    needed so that the coefficient stays >= 0.05 at every corner of the xi box (Legendre:
+    abar - sqrt(3) sum_k |c_k| >= 0.05 per cell)."""
+    import numpy as np
+    from paper_1304_1755_gb300 import inputs, sg
+    out = []
+    for s in inputs.batch_systems(wl["batch_seed"], wl["count"]):
+        unit, _ = sg.sg_kl_coef(s["n"], s["M"], 1.0)
+        worst = float(np.max(np.sqrt(3.0) * np.abs(unit[1:]).sum(axis=0)))
+        sigma = min(s["sigma"], 0.95 / worst)
+        coef = unit.copy()
+        coef[0] = 1.0
+        coef[1:] *= sigma
+        n = s["n"]
+        F = np.zeros(math.comb(s["M"] + s["p"], s["p"]) * (n - 2) ** 2)
+        F[:(n - 2) ** 2] = 1.0 / (n - 1) ** 2
+        out.append(dict(s, sigma=sigma, sigma_drawn=s["sigma"], coef=coef, F=F))
+    return out
+
+
+def run_c5(args, wl, rank, world):
+    """Aggregate unknowns solved per second for the uneven batch, all systems at once
+    (sg_solve_batch, nstreams worker streams) against one at a time (sg_solve in a loop)."""
+    import torch
+    from paper_1304_1755_gb300 import build as B
+    from paper_1304_1755_gb300 import sg
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if not os.path.exists(sg.LIB_PATH):
+        B.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    systems = c5_systems(wl)
+    hs = [sg.Handle(s["n"], s["M"], s["p"], wl["family"], s["coef"], stream=stream) for s in systems]
+    t0 = time.perf_counter()
+    for h in hs:
+        h.autotune()
+    tune_s = time.perf_counter() - t0
+    Fs = [torch.as_tensor(s["F"]).cuda() for s in systems]
+    Us = [torch.zeros_like(F) for F in Fs]
+    unknowns = sum(int(F.numel()) for F in Fs)
+    opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=wl["restart"], maxit=400, tol=wl["tol"],
+                pc_prec=wl["pc_prec"], reorth=0, arith=sg.ARITH_F64)
+
+    def one_at_a_time():
+        return [h.solve(F, U, **opts) for h, F, U in zip(hs, Fs, Us)]
+
+    def batched():
+        return sg.solve_batch(hs, Fs, Us, nstreams=wl["nstreams"], **opts)
+
+    for _ in range(args.warmup):
+        one_at_a_time()
+        batched()
+    torch.cuda.synchronize()
+    for h in hs:
+        h.timing_enable(True)
+    barrier()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            infos = batched()
+        torch.cuda.synchronize()
+        barrier()
+        t_batch = (time.perf_counter() - t0) / args.steps
+    clocks = clk.summary()
+    ph = [h.timing_read() for h in hs]
+    for h in hs:
+        h.timing_enable(False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        infos1 = one_at_a_time()
+    torch.cuda.synchronize()
+    t_seq = (time.perf_counter() - t0) / args.steps
+    t_batch, t_seq = max_over_ranks([t_batch, t_seq])
+    launches = sum(sum(l) for _, l in ph) // args.steps
+    op_ms = sum(m[0] for m, _ in ph) / args.steps
+    op_launches = sum(l[0] for _, l in ph) // args.steps
+    # end to end through the C ABI with host (pinned) buffers: sg_solve stages them per system
+    Fh = [torch.as_tensor(s["F"]).pin_memory() for s in systems]
+    Uh = [torch.zeros_like(F).pin_memory() for F in Fh]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sg.solve_batch(hs, [F.numpy() for F in Fh], [U.numpy() for U in Uh], nstreams=wl["nstreams"], **opts)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    nbytes = 8 * unknowns
+    out = {
+        "metric": C5_METRIC,
+        "value": round(world * unknowns / t_batch, 1),
+        "unit": "unknowns/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_batch * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 Krylov, preconditioner f32",
+        "data": "synthetic (seeded uneven batch: KL coefficients, Legendre chaos, f = 1)",
+        "config": {"workload": wl["name"], "systems": len(hs), "unknowns": unknowns, "nstreams": wl["nstreams"],
+                   "sigma_lowered": sum(1 for s in systems if s["sigma"] < s["sigma_drawn"]),
+                   "l2": "working set of the batch larger than L2, no flush"},
+        "one_at_a_time": {"value": round(world * unknowns / t_seq, 1), "unit": "unknowns/s",
+                          "ms_per_step": round(t_seq * 1e3, 3)},
+        "batch_speedup": round(t_seq / t_batch, 3),
+        "iterations": [i.iters for i in infos],
+        "relres_true_max": max(i.relres_true for i in infos),
+        "agree_with_one_at_a_time": all(i.iters == j.iters for i, j in zip(infos, infos1)),
+        "autotune_s": round(tune_s, 3),
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(world * unknowns / t_e2e, 1), "unit": "unknowns/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "clocks": clocks,
+    }
+    fl = sum(k1_flops(dict(n=s["n"], M=s["M"], p=s["p"]), False) for s in systems)   # one apply per system
+    apply_ms = op_ms / max(op_launches, 1) * len(hs)
+    out["roofline"] = {"kernel": "k_apply<ArF64> (outer SG operator, FP64), summed over the batch's systems",
+                       "bound": "alu", "achieved": round(fl / (apply_ms * 1e-3) / 1e12, 3), "peak": 1.25,
+                       "unit": "TFLOP/s", "frac": round(fl / (apply_ms * 1e-3) / 1e12 / 1.25, 4), "traffic": None,
+                       "peak_source": "nominal FP64 1.25 TFLOP/s (profiling recipe)",
+                       "note": "launch time measured per system with events; concurrent streams overlap"}
+    for h in hs:
+        h.close()
+    return out
+
+
+class CpuSampleBatch:
+    """The oracle on a bounded sample of the uneven batch: its systems on the 65 x 65 grid, solved
+    one after another by the oracle's block-triangular FGMRES, until about 20 s have been spent;
+    the metric is unknowns solved per second."""
+
+    def __init__(self, wl, budget_s=20.0):
+        from oracle import mg, precond, sg as osg
+        self.wl, self.budget_s = wl, budget_s
+        self.items = []
+        for s in c5_systems(wl):
+            if s["n"] != 65:
+                continue
+            sysm = osg.build(s["n"], s["M"], s["p"], wl["family"], s["coef"])
+            A = osg.assemble(sysm)
+            solver = precond.DiagSolver(sysm.K[0], mg.Hierarchy(sysm.K[0], s["n"]))
+            self.items.append((sysm, A, osg.rhs(sysm), solver))
+
+    def run(self):
+        from oracle import krylov, precond
+        t0 = time.perf_counter()
+        done = 0
+        count = 0
+        for sysm, A, F, solver in self.items:
+            krylov.gmres(lambda v: A @ v, lambda r: precond.block_tri_inv(sysm, solver, r), F, tol=self.wl["tol"],
+                         restart=self.wl["restart"], maxit=400, flexible=True)
+            done += sysm.P * sysm.Nx
+            count += 1
+            if time.perf_counter() - t0 > self.budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return done / dt, f"oracle BT-FGMRES({self.wl['restart']}) to {self.wl['tol']:g} on {count} of the batch's " \
+                          f"65x65 systems ({done} unknowns) in {dt:.1f} s, one after another"
 
 
 class CpuSample:
@@ -285,6 +619,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--arith", default="df64", choices=["f64", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", 0))
@@ -292,13 +627,60 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        if args.workload == "c4":
+            from oracle import adjoint as oadj, sg as osg
+            from paper_1304_1755_gb300 import inputs
+            from oracle import kl
+            nc = 33
+            unit = kl.kl_coefficients(nc, wl["M"], 1.0)
+            coef = unit.copy()
+            coef[0] = inputs.lognormal_cells(wl["abar_seed"], nc, 0.2)
+            coef[1:] *= wl["sigma"]
+            sysm = osg.build(nc, wl["M"], wl["p"], wl["family"], coef)
+            times = []
+            for k in range(args.warmup + args.steps):
+                t0 = time.perf_counter()
+                oadj.solve_and_gradients(sysm, unit)
+                if k >= args.warmup:
+                    times.append(time.perf_counter() - t0)
+            N = (wl["n"] - 2) ** 2 * math.comb(wl["M"] + wl["p"], wl["p"])
+            v = statistics.median(times) * N / (sysm.P * sysm.Nx)
+            sample = (f"oracle adjoint gradient (sparse direct forward and adjoint solves) on the {nc}x{nc} copy "
+                      f"({sysm.P * sysm.Nx} unknowns) in {statistics.median(times):.2f} s; scaled by unknowns")
+            print(json.dumps({"impl": "reference", "metric": "time per adjoint gradient dJ/d(abar, sigma) (forward + "
+                              "transpose block-tri FGMRES+MG to 1e-8)", "value": round(v, 3), "unit": "s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                              "config": {"workload": wl["name"]},
+                              "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
+                                               "sample": sample},
+                              "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}))
+            return
+        if args.workload == "c5":
+            smp = CpuSampleBatch(wl)
+            vals = []
+            for k in range(args.warmup + args.steps):
+                v, sample = smp.run()
+                if k >= args.warmup:
+                    vals.append(v)
+            v = statistics.median(vals)
+            print(json.dumps({"impl": "reference", "metric": C5_METRIC, "value": round(v, 1), "unit": "unknowns/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                              "config": {"workload": wl["name"]},
+                              "cpu_baseline": {"value": round(v, 1), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                                               "sample": sample},
+                              "e2e": {"value": round(v, 1), "unit": "unknowns/s", "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}))
+            return
         smp = CpuSample(wl)
         times = []
         for k in range(args.warmup + args.steps):
             dt, its = smp.run()
             if k >= args.warmup:
                 times.append(dt)
-        n, P = wl["n"], __import__("math").comb(wl["M"] + wl["p"], wl["p"])
+        n, P = wl["n"], math.comb(wl["M"] + wl["p"], wl["p"])
         unknowns = (n - 2) ** 2 * P
         # the oracle's own iteration count at the copy, scaled to the workload's unknowns
         v = statistics.median(times) * unknowns / smp.unknowns
@@ -315,6 +697,24 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.workload == "c4":
+        out = run_c4(args, wl, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    if args.workload == "c5":
+        out = run_c5(args, wl, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            v, sample = CpuSampleBatch(wl).run()
+            out["cpu_baseline"] = {"value": round(v, 1), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                                   "sample": sample}
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     out = run_ours(args, wl, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = CpuSample(wl)

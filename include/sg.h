@@ -195,6 +195,27 @@ int sg_vcycle_static(sg_handle h, const double* B, void* X, int nblocks, int pre
  * iterate). */
 int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info);
 
+/* Solve nsys independent systems, each with its own handle (any mix of grids, M and p;
+ * the batched form of the method's solve, Sec. 4.2 / 6, for many problems at once).
+ * hs[s], F[s], U[s] as in sg_solve (device pointers); the same opts for every system.
+ * nstreams (1..64) worker threads each drive one CUDA stream created for the call and
+ * take the systems largest first; each handle's own stream is restored afterwards.
+ * infos (may be NULL) receives one sg_solve_info per system, with status set to that
+ * system's sg_solve result.  Returns SG_OK or the first failing system's status.
+ * Handles must be distinct and not used by other calls while the batch runs. */
+int sg_solve_batch(sg_handle* hs, const double* const* F, double* const* U, int nsys, const sg_solve_opts* opts,
+                   sg_solve_info* infos, int nstreams);
+
+/* Choose the operator kernel's tile (the number of grid rows a warp walks) for this
+ * problem by timing the candidates 4, 8, 16, 32 and 64 on the device (a tuning step of
+ * this implementation; the paper has no counterpart).  which: bit 0 FP64 arithmetic,
+ * bit 1 FP32, bit 2 double-float; 0 = all.  Allocates two temporary vectors of P*N_x
+ * doubles and runs about sixty operator applications on the handle's stream; the
+ * choice is kept in the handle and cached for the process by (n, M, p, couplings,
+ * mean), so later handles of the same shape are tuned without timing.  Without this
+ * call the tile is 16 rows. */
+int sg_autotune(sg_handle h, int which);
+
 /* Objective J = E[Q] + Var[Q]/2, Q = int u dx: J = m^T U_0 + 1/2 sum_{i>=1}(m^T U_i)^2
  * with m_s = h^2, and its gradient G = dJ/dU (device U, G; J host). */
 int sg_objective(sg_handle h, const double* U, double* J, double* G);

@@ -114,7 +114,10 @@ int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec
 
 // Krylov vectors use the padded length Np (multiple of 64) with zero padding, so the
 // Gram-Schmidt kernels can run 16-byte loads over whole vectors.
-int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec) {
+// Krylov workspace.  layout: 0 = FP64 basis, 1 = double-float basis, -1 = the basis is not
+// used.  The Gram-Schmidt kernels stream whole padded vectors and rely on zero padding, which
+// the other layout's vectors do not leave behind, so a change of layout clears the basis.
+int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec, int layout = -1) {
   const size_t N = h->Nx * (size_t)h->P, Np = h->Np;
   if (h->kv_cap < nv) {
     cudaFree(h->kv);
@@ -123,6 +126,11 @@ int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec) {
     if (cudaMalloc(&h->kv, sizeof(double) * Np * nv) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc Krylov basis");
     SG_CUDA(h, cudaMemsetAsync(h->kv, 0, sizeof(double) * Np * nv, h->stream));
     h->kv_cap = nv;
+    h->kv_layout = layout;
+  }
+  if (layout >= 0 && h->kv_layout != layout) {
+    SG_CUDA(h, cudaMemsetAsync(h->kv, 0, sizeof(double) * Np * h->kv_cap, h->stream));
+    h->kv_layout = layout;
   }
   if (h->kz_cap < nz || h->kz_prec != zprec) {
     cudaFree(h->kz);
@@ -155,7 +163,7 @@ struct OpsF64 {
   bool flexible;
   double* V;
   int init() {
-    int rc = ensure_krylov(h, o.restart + 1, flexible ? o.restart : 1, o.pc_prec);
+    int rc = ensure_krylov(h, o.restart + 1, flexible ? o.restart : 1, o.pc_prec, 0);
     V = h->kv;
     return rc;
   }
@@ -165,11 +173,10 @@ struct OpsF64 {
   int zero_solution() { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
   int residual(bool) { return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F); }
   int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
-  int scale(int l, double s) { return vec_scale(h, v(l), v(l), N, s); }
   int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
   int apply(int j) { return apply_f64(h, 0, o.pc_prec, z(j), SG_F64, v(j + 1), nullptr); }
   int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
-  int axpys(int j) { return vec_axpys_norm(h, V, h->Np, j + 1, h->red_out, v(j + 1), h->Np, nullptr); }
+  int axpys(int j, const double* c) { return vec_axpys_norm(h, V, h->Np, j + 1, c, v(j + 1), h->Np, nullptr); }
   int update(int k, const double* y) {
     if (flexible) return vec_update(h, U, o.pc_prec, h->kz, N, k, y, N);
     double* t = h->ktmp;
@@ -194,7 +201,7 @@ struct OpsDF {
   int init() {
     if (o.pc_prec != SG_F32 && o.pc_prec != SG_BF16)
       return sg_fail(h, SG_E_ARG, "double-float mode needs an FP32 or BF16 preconditioner");
-    int rc = ensure_krylov(h, o.restart + 1, o.restart, o.pc_prec);
+    int rc = ensure_krylov(h, o.restart + 1, o.restart, o.pc_prec, 1);
     if (rc) return rc;
     const size_t Np = h->Np;
     V = (float*)h->kv;
@@ -231,18 +238,21 @@ struct OpsDF {
     if ((rc = df_dots(h, nullptr, 0, 0, v(l), h->Np, true))) return rc;
     return copy_red(h, 0, 1, out);
   }
-  int scale(int l, double s) { return df_scale(h, v(l), h->Np, s); }
   int precond(int j) { return apply_precond(h, o.precond, SG_F32, v(j), z(j), o.pc_prec, o.transpose); }
   int apply(int j) {
     return launch_apply(h, 0, o.pc_prec, z(j), 0, SG_DF64, v(j + 1), h->Np, SG_DF64, nullptr, 0, 0, h->P, 0, 0,
                         SG_DF64);
   }
   int dots(int j, bool ww) { return df_dots(h, V, 2 * h->Np, j + 1, v(j + 1), h->Np, ww); }
-  int axpys(int j) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, h->red_out, v(j + 1), h->Np); }
+  int axpys(int j, const double* c) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, c, v(j + 1), h->Np); }
   int update(int k, const double* y) { return df_update(h, Ud, h->Np, o.pc_prec, h->kz, N, k, y, N); }
   int finish() { return df_to_f64(h, Ud, U, N, h->Np); }
 };
 
+// The basis is normalised lazily: the stored vector l is v_l / s_l with s_l = 1 / ||stored
+// v_l||, and every consumer folds s_l into its scalars (the preconditioner and the operator
+// are linear, so z_j and A z_j carry the factor s_j), which saves one read-write pass over
+// a basis vector per iteration.
 template <class Ops>
 int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& info) {
   const int m = o.restart;
@@ -256,13 +266,13 @@ int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& in
     info.relres_true = info.relres_est = 0;
     return ops.zero_solution();
   }
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), h2(m + 2), y(m);
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), dv(m + 2), d2(m + 2), coef(m + 1), y(m), sc(m + 1);
   int its = 0;
   bool u_zero = !o.x0_given;
   for (;;) {
     {
       PhaseScope ps(h, 3);
-      if ((rc = ops.residual(u_zero))) return rc;   // v_0 = F - A U, the IEEE FP64 true residual
+      if ((rc = ops.residual(u_zero))) return rc;   // stored v_0 = F - A U, the IEEE FP64 true residual
     }
     double b2 = 0;
     if ((rc = ops.norm2(0, &b2))) return rc;
@@ -275,48 +285,53 @@ int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& in
       break;
     }
     if (its >= o.maxit) { info.iters = its; ops.finish(); return SG_E_NOCONV; }
-    if ((rc = ops.scale(0, 1.0 / beta))) return rc;
+    sc[0] = 1.0 / beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
     for (int j = 0; j < m; ++j) {
       {
         PhaseScope ps(h, 1);
-        if ((rc = ops.precond(j))) return rc;                  // z_j = B^{-1} v_j
+        if ((rc = ops.precond(j))) return rc;                  // z_j / s_j = B^{-1} (stored v_j)
       }
       {
         PhaseScope ps(h, 0);
-        if ((rc = ops.apply(j))) return rc;                    // w = A z_j  (stored in v_{j+1})
+        if ((rc = ops.apply(j))) return rc;                    // w / s_j = A z_j / s_j, stored in v_{j+1}
       }
-      // classical Gram-Schmidt: h = V^T w (with w.w), w -= V h, ||w||^2
+      // classical Gram-Schmidt on the stored vectors: d = V^T w (and w.w), w -= V (s^2 d), ||w||^2
       {
         PhaseScope ps(h, 2);
         if ((rc = ops.dots(j, true))) return rc;
       }
-      if ((rc = copy_red(h, 0, j + 2, hcol.data()))) return rc;
+      if ((rc = copy_red(h, 0, j + 2, dv.data()))) return rc;
+      for (int i = 0; i <= j; ++i) coef[i] = sc[i] * sc[i] * dv[i];
+      if ((rc = upload_red(h, 3, coef.data(), j + 1))) return rc;
       double nrm2 = 0;
       {
         PhaseScope ps(h, 2);
-        if ((rc = ops.axpys(j))) return rc;
+        if ((rc = ops.axpys(j, red_slot(h, 3)))) return rc;
       }
       if ((rc = copy_red(h, 1, 1, &nrm2))) return rc;
-      if (o.reorth && nrm2 < 0.5 * hcol[j + 1]) {
+      if (o.reorth && nrm2 < 0.5 * dv[j + 1]) {
         {
           PhaseScope ps(h, 2);
           if ((rc = ops.dots(j, false))) return rc;
         }
-        if ((rc = copy_red(h, 0, j + 1, h2.data()))) return rc;
+        if ((rc = copy_red(h, 0, j + 1, d2.data()))) return rc;
+        for (int i = 0; i <= j; ++i) coef[i] = sc[i] * sc[i] * d2[i];
+        if ((rc = upload_red(h, 3, coef.data(), j + 1))) return rc;
         {
           PhaseScope ps(h, 2);
-          if ((rc = ops.axpys(j))) return rc;
+          if ((rc = ops.axpys(j, red_slot(h, 3)))) return rc;
         }
         if ((rc = copy_red(h, 1, 1, &nrm2))) return rc;
-        for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
+        for (int i = 0; i <= j; ++i) dv[i] += d2[i];
       }
-      const double hn = std::sqrt(nrm2);
+      const double hn = sc[j] * std::sqrt(nrm2);
       for (int i = 0; i <= j; ++i) {
-        if (!std::isfinite(hcol[i])) return sg_fail(h, SG_E_NONFINITE, "non-finite Hessenberg entry");
-        H[i * m + j] = hcol[i];
+        const double hij = sc[i] * sc[j] * dv[i];
+        if (!std::isfinite(hij)) return sg_fail(h, SG_E_NONFINITE, "non-finite Hessenberg entry");
+        H[i * m + j] = hij;
       }
       if (!std::isfinite(hn)) return sg_fail(h, SG_E_NONFINITE, "non-finite Arnoldi norm");
       H[(j + 1) * m + j] = hn;
@@ -337,13 +352,14 @@ int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& in
       k = j + 1;
       info.relres_est = std::fabs(g[j + 1]) / bnorm;
       if (hn == 0.0 || std::fabs(g[j + 1]) <= o.tol * bnorm || its >= o.maxit) break;
-      if ((rc = ops.scale(j + 1, 1.0 / hn))) return rc;
+      sc[j + 1] = 1.0 / std::sqrt(nrm2);
     }
     for (int i = k - 1; i >= 0; --i) {   // back substitution H y = g
       double s = g[i];
       for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
       y[i] = s / H[i * m + i];
     }
+    for (int i = 0; i < k; ++i) y[i] *= sc[i];    // stored z_i = z_i / s_i
     {
       PhaseScope ps(h, 3);
       if ((rc = ops.update(k, y.data()))) return rc;

@@ -13,10 +13,15 @@
 // hg = ta - tb + tc - td and scatters  A = d1/2, B = d2/2, C = hg/6  to the corners:
 // a += A + C, b += B - C, c += C - A, d += -B - C.
 //
-// One thread per cell: a CTA owns 32 x 8 cells and produces the 31 x 7 nodes
-// whose four cells it holds (cell results meet in shared memory), looping over
-// ROWS output rows.  The 1-D grid enumerates (tile, row group) with row groups
-// fastest, so a tile's input columns are reused from L2 by neighbouring CTAs.
+// One lane per cell: a warp owns 32 consecutive cells of a cell row and walks up a
+// strip of cell rows for one output row i.  Per cell row and coupling it loads the two
+// right-hand corners of its cell (the left ones come from the neighbouring lane by a
+// shuffle), forms the cell's features, and then finishes the node on its cell's SW
+// corner from the features of the four cells around it: the two of this lane (this cell
+// row and the previous one, kept in registers) and the two of the lane on its left,
+// which sends their combined contribution in one shuffle.  Lane 0 only supplies its
+// cell to lane 1, so warps advance by 31 cells.  No shared memory, no block barriers
+// in the main loop; the coupling table of the row is staged in shared memory once.
 //
 // Arithmetic policies: FP32, FP64 (IEEE double) and DF (double-float, see df64.cuh;
 // used where FP64-class accuracy is needed at FP32 throughput).
@@ -26,10 +31,9 @@
 #include "sg_internal.h"
 
 namespace {
-constexpr int CXN = 32, CYN = 8, NT = CXN * CYN;   // cells per CTA
-constexpr int OXN = CXN - 1, OYN = CYN - 1;        // output nodes per CTA
-constexpr int ROWS = 4;
-constexpr int MAXT = 16;                            // staged coupling terms per row (more: read from global)
+constexpr int WARPS = 8, NT = 32 * WARPS;          // warps per CTA (all on the same output row)
+constexpr int STRIP_DEFAULT = 16;                   // node rows per warp strip (tunable: sg_autotune)
+constexpr int MAXT = 40;                            // coupling terms per row: at most 1 + 2M (M <= 16 at set-up)
 
 struct ApplyArgs {
   const void* X;
@@ -51,7 +55,7 @@ struct ApplyArgs {
   const df2* gdf;
   int row0, nrows, ybase, rbase, n, m;
   size_t Nx, Nc;
-  int tiles_x, ngroups;
+  int nwx, nstrips, strip;   // warp columns (31 cells each), strips per output row, node rows per strip
 };
 
 // ---- storage access --------------------------------------------------------
@@ -107,10 +111,14 @@ struct ArF32 {
   static constexpr bool kUsesTable = false;
   typedef float T;
   typedef float Acc;
-  static __device__ __forceinline__ T weight(const ApplyArgs& a, int k, size_t e, int t) {
-    return a.c32[(size_t)k * a.Nc + e] * a.g32[t];
+  typedef float G;
+  static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.g32[t]; }
+  template <bool WT>
+  static __device__ __forceinline__ T weight(const ApplyArgs& a, long long wo, size_t e, G g) {
+    return a.c32[wo + e] * g;
   }
   static __device__ __forceinline__ Acc zero() { return 0.f; }
+  static __device__ __forceinline__ T wzero() { return 0.f; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { s = fmaf(w, z, s); }
   static __device__ __forceinline__ void fma(Acc& s, T w, double z) { s = fmaf(w, (float)z, s); }
   static __device__ __forceinline__ void fma(Acc& s, T w, df2 z) { s = fmaf(w, z.hi, s); }
@@ -128,10 +136,14 @@ struct ArF64 {
   static constexpr bool kUsesTable = false;
   typedef double T;
   typedef double Acc;
-  static __device__ __forceinline__ T weight(const ApplyArgs& a, int k, size_t e, int t) {
-    return a.c64[(size_t)k * a.Nc + e] * a.g64[t];
+  typedef double G;
+  static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.g64[t]; }
+  template <bool WT>
+  static __device__ __forceinline__ T weight(const ApplyArgs& a, long long wo, size_t e, G g) {
+    return a.c64[wo + e] * g;
   }
   static __device__ __forceinline__ Acc zero() { return 0.0; }
+  static __device__ __forceinline__ T wzero() { return 0.0; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { s = ::fma(w, (double)z, s); }
   static __device__ __forceinline__ void fma(Acc& s, T w, double z) { s = ::fma(w, z, s); }
   static __device__ __forceinline__ void fma(Acc& s, T w, df2 z) { s = ::fma(w, (double)z.hi + (double)z.lo, s); }
@@ -150,11 +162,16 @@ struct ArDF {
   typedef dacc Acc;
   // with the weight table, k is the term's weight slot (precomputed c_k(e) gamma products)
   static constexpr bool kUsesTable = true;
-  static __device__ __forceinline__ T weight(const ApplyArgs& a, int k, size_t e, int t) {
-    if (a.wdf) return a.wdf[(size_t)k * a.Nc + e];
-    return df_mul(a.cdf[(size_t)k * a.Nc + e], a.gdf[t]);
+  typedef df2 G;
+  static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.gdf[t]; }
+  // WT: with the table, wo addresses the precomputed product c_k(e) gamma of the term's slot
+  template <bool WT>
+  static __device__ __forceinline__ T weight(const ApplyArgs& a, long long wo, size_t e, G g) {
+    if (WT) return a.wdf[wo + e];
+    return df_mul(a.cdf[wo + e], g);
   }
   static __device__ __forceinline__ Acc zero() { return dacc_zero(); }
+  static __device__ __forceinline__ T wzero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { dacc_fma(s, w, z); }
   static __device__ __forceinline__ void fma(Acc& s, T w, df2 z) { dacc_fma(s, w, z); }
   static __device__ __forceinline__ void fma(Acc& s, T w, double z) { dacc_fma(s, w, df_from_double(z)); }
@@ -245,120 +262,148 @@ template <> struct Store<DFS> {
   static __device__ __forceinline__ void put(void* p, size_t lo, size_t i, float v) { put(p, lo, i, df2{v, 0.f}); }
 };
 
-// R - y in the policy's arithmetic (R stored as TR)
+// R - y in the policy's arithmetic (R stored as TR).  ld() fetches R's value early (the
+// kernel issues it before the coupling loads so its latency overlaps them), f() combines.
 struct NoR {};
 template <class AR, typename TR> struct Epi {
-  template <typename T> static __device__ __forceinline__ T f(const void*, size_t, size_t, T y) { return y; }
+  typedef int Raw;
+  static __device__ __forceinline__ Raw ld(const void*, size_t, size_t) { return 0; }
+  template <typename T> static __device__ __forceinline__ T f(Raw, T y) { return y; }
 };
 template <> struct Epi<ArF32, double> {
-  static __device__ __forceinline__ float f(const void* R, size_t, size_t i, float y) { return (float)((const double*)R)[i] - y; }
+  typedef double Raw;
+  static __device__ __forceinline__ Raw ld(const void* R, size_t, size_t i) { return ((const double*)R)[i]; }
+  static __device__ __forceinline__ float f(Raw r, float y) { return (float)r - y; }
 };
 template <> struct Epi<ArF32, DFS> {
-  static __device__ __forceinline__ float f(const void* R, size_t, size_t i, float y) { return ((const float*)R)[i] - y; }
+  typedef float Raw;
+  static __device__ __forceinline__ Raw ld(const void* R, size_t, size_t i) { return ((const float*)R)[i]; }
+  static __device__ __forceinline__ float f(Raw r, float y) { return r - y; }
 };
 template <> struct Epi<ArF32, float> {
-  static __device__ __forceinline__ float f(const void* R, size_t, size_t i, float y) { return ((const float*)R)[i] - y; }
+  typedef float Raw;
+  static __device__ __forceinline__ Raw ld(const void* R, size_t, size_t i) { return ((const float*)R)[i]; }
+  static __device__ __forceinline__ float f(Raw r, float y) { return r - y; }
 };
 template <> struct Epi<ArF64, double> {
-  static __device__ __forceinline__ double f(const void* R, size_t, size_t i, double y) { return ((const double*)R)[i] - y; }
+  typedef double Raw;
+  static __device__ __forceinline__ Raw ld(const void* R, size_t, size_t i) { return ((const double*)R)[i]; }
+  static __device__ __forceinline__ double f(Raw r, double y) { return r - y; }
 };
 template <> struct Epi<ArDF, DFS> {
-  static __device__ __forceinline__ df2 f(const void* R, size_t lo, size_t i, df2 y) {
-    return df_sub(df2{((const float*)R)[i], ((const float*)R)[i + lo]}, y);
+  typedef df2 Raw;
+  static __device__ __forceinline__ Raw ld(const void* R, size_t lo, size_t i) {
+    return df2{((const float*)R)[i], ((const float*)R)[i + lo]};
   }
+  static __device__ __forceinline__ df2 f(Raw r, df2 y) { return df_sub(r, y); }
 };
 template <> struct Epi<ArDF, double> {
-  static __device__ __forceinline__ df2 f(const void* R, size_t, size_t i, df2 y) {
-    return df_sub(df_from_double(((const double*)R)[i]), y);
-  }
+  typedef double Raw;
+  static __device__ __forceinline__ Raw ld(const void* R, size_t, size_t i) { return ((const double*)R)[i]; }
+  static __device__ __forceinline__ df2 f(Raw r, df2 y) { return df_sub(df_from_double(r), y); }
 };
 
-template <class AR, typename TXS, typename TYS, typename TRS>
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ df2 shfl_up1(df2 v) {
+  return {__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+}
+
+// The row's couplings as shared-memory tables: column offset j N_x, weight-row offset
+// (mode k, or table slot) times N_c, and the coupling value.
+template <class AR> struct RowTerms {
+  long long xo[MAXT];
+  long long wo[MAXT];
+  typename AR::G g[MAXT];
+};
+
+template <class AR, bool WT, typename TXS, typename TYS, typename TRS>
 __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   typedef typename AR::T T;
   typedef typename AR::Acc Acc;
   typedef Load<TXS> LX;
-  __shared__ T sA[NT], sB[NT], sC[NT];
-  const int tid = threadIdx.x;
-  const int tile = blockIdx.x / a.ngroups, group = blockIdx.x % a.ngroups;
-  const int X0 = (tile % a.tiles_x) * OXN, Y0 = (tile / a.tiles_x) * OYN;   // first interior node of the tile
-  const int cx = X0 + (tid % CXN), cy = Y0 + (tid / CXN);                   // this thread's cell
-  const int n = a.n, m = a.m;
-  const bool cell_ok = cx <= n - 2 && cy <= n - 2;
-  const size_t e = (size_t)cx + (size_t)cy * (n - 1);
-  // corner vertices: a = (cx, cy), b = (cx+1, cy), c = (cx+1, cy+1), d = (cx, cy+1)
-  const bool ina = cx >= 1 && cx <= n - 2 && cy >= 1 && cy <= n - 2;
-  const bool inb = cx + 1 <= n - 2 && cy >= 1 && cy <= n - 2;
-  const bool inc = cx + 1 <= n - 2 && cy + 1 <= n - 2;
-  const bool ind = cx >= 1 && cx <= n - 2 && cy + 1 <= n - 2;
-  const long ia = (long)(cx - 1) + (long)(cy - 1) * m;   // interior index of corner a (may be < 0 when unused)
-  const int rbeg = a.row0 + group * ROWS;
-  const int rend = min(rbeg + ROWS, a.row0 + a.nrows);
-  const int ox = tid % OXN, oy = tid / OXN;
-  // stage the coupling terms of this CTA's rows in shared memory (one round trip instead of
-  // one per term): column j and mode k
-  __shared__ int s_tj[ROWS * MAXT], s_tk[ROWS * MAXT];
-  const int tall0 = a.row_ptr[rbeg], tall1 = a.row_ptr[rend];
-  const bool staged = tall1 - tall0 <= ROWS * MAXT;
-  if (staged) {
-    for (int t = tall0 + tid; t < tall1; t += NT) {
-      s_tj[t - tall0] = a.tj[t];
-      s_tk[t - tall0] = (AR::kUsesTable && a.wdf) ? a.ws[t] : a.tk[t];
-    }
-    __syncthreads();
+  typedef typename LX::Z Z;
+  typedef Epi<AR, TRS> E;
+  __shared__ RowTerms<AR> rt;
+  const int i = a.row0 + blockIdx.y;                       // output row of this CTA
+  const int t0 = a.row_ptr[i];
+  const int nt = a.row_ptr[i + 1] - t0;                    // <= MAXT (checked at set-up)
+  for (int t = threadIdx.x; t < nt; t += NT) {
+    rt.xo[t] = (long long)a.tj[t0 + t] * (long long)a.Nx;
+    rt.wo[t] = (long long)(WT ? a.ws[t0 + t] : a.tk[t0 + t]) * (long long)a.Nc;
+    rt.g[t] = AR::gval(a, t0 + t);
   }
-  for (int i = rbeg; i < rend; ++i) {
-    const int t0 = a.row_ptr[i], t1 = a.row_ptr[i + 1];
+  __syncthreads();
+  const int gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  if (gw >= a.nwx * a.nstrips) return;                     // whole warps only
+  const int lane = threadIdx.x & 31;
+  const int n = a.n, m = a.m;
+  const int cx = 31 * (gw % a.nwx) + lane;                 // cell column = vertex column of its SW corner
+  const int cy0 = a.strip * (gw / a.nwx);                  // first cell row (primes the window)
+  const int cy1 = min(cy0 + a.strip, n - 2);               // last cell row = last node row of the strip
+  const bool okl = cx >= 1 && cx <= n - 2;                 // left corners (vertex column cx) interior
+  const bool okr = cx + 1 <= n - 2;                        // right corners (vertex column cx + 1) interior
+  const bool node_col = lane >= 1 && cx <= n - 2;          // this lane finishes node (cx, cy)
+  const int cxw = min(cx, n - 2);                          // weight column (cells beyond the grid have zero corners)
+  const size_t yoff = (size_t)(i - a.ybase) * a.Nx, roff = (size_t)(i - a.rbase) * a.Nx;
+  T Ap = AR::wzero(), Bp = AR::wzero(), Cp = AR::wzero();   // features of cell (cx, cy - 1)
+  for (int cy = cy0; cy <= cy1; ++cy) {
+    const bool out = node_col && cy > cy0;                 // node (cx, cy): 1 <= cy <= n - 2 here
+    const size_t s_node = (size_t)(cx - 1) + (size_t)(cy - 1) * m;
+    typename E::Raw rv;
+    if (out) rv = E::ld(a.R, a.rlo, roff + s_node);
+    const bool lo_ok = cy >= 1, hi_ok = cy + 1 <= n - 2;
+    const bool oka = okl && lo_ok, okb = okr && lo_ok, okc = okr && hi_ok, okd = okl && hi_ok;
+    const long long ia = (long long)(cx - 1) + (long long)(cy - 1) * m;   // interior index of vertex (cx, cy)
+    const size_t e = (size_t)cxw + (size_t)cy * (n - 1);
     typename AR::State st;
     AR::init(st);
-    if (cell_ok) {
 #pragma unroll 2
-      for (int t = t0; t < t1; ++t) {
-        const int jj = staged ? s_tj[t - tall0] : a.tj[t];
-        const int kk = staged ? s_tk[t - tall0] : ((AR::kUsesTable && a.wdf) ? a.ws[t] : a.tk[t]);
-        const size_t base = (size_t)jj * a.Nx;
-        const T w = AR::weight(a, kk, e, t);
-        const typename LX::Z za = ina ? LX::at(a.X, a.xlo, base + ia) : LX::zero();
-        const typename LX::Z zb = inb ? LX::at(a.X, a.xlo, base + ia + 1) : LX::zero();
-        const typename LX::Z zc = inc ? LX::at(a.X, a.xlo, base + ia + 1 + m) : LX::zero();
-        const typename LX::Z zd = ind ? LX::at(a.X, a.xlo, base + ia + m) : LX::zero();
-        AR::term(st, w, za, zb, zc, zd);
-      }
+    for (int t = 0; t < nt; ++t) {
+      const long long q = rt.xo[t] + ia;
+      const T w = AR::template weight<WT>(a, rt.wo[t], e, rt.g[t]);
+      const Z za = oka ? LX::at(a.X, a.xlo, (size_t)q) : LX::zero();
+      const Z zb = okb ? LX::at(a.X, a.xlo, (size_t)(q + 1)) : LX::zero();
+      const Z zc = okc ? LX::at(a.X, a.xlo, (size_t)(q + 1 + m)) : LX::zero();
+      const Z zd = okd ? LX::at(a.X, a.xlo, (size_t)(q + m)) : LX::zero();
+      AR::term(st, w, za, zb, zc, zd);
     }
-    AR::features(st, sA[tid], sB[tid], sC[tid]);
-    __syncthreads();
-    if (tid < OXN * OYN) {
-      const int ix = X0 + ox, iy = Y0 + oy;
-      if (ix < m && iy < m) {
-        const int cSWn = ox + oy * CXN;          // cell SW of the node: node is its NE corner (c)
-        const int cSEn = cSWn + 1;               // node is its NW corner (d)
-        const int cNWn = cSWn + CXN;             // node is its SE corner (b)
-        const int cNEn = cSWn + CXN + 1;         // node is its SW corner (a)
+    T Ac, Bc, Cc;
+    AR::features(st, Ac, Bc, Cc);
+    if (cy > cy0) {
+      // this lane's cells seen from node (cx + 1, cy): SE corner of cell (cx, cy) and NE corner of
+      // cell (cx, cy - 1); sent to the right neighbour
+      Acc u = AR::zero();
+      AR::acc_add(u, Bc);
+      AR::acc_sub(u, Cc);
+      AR::acc_add(u, Cp);
+      AR::acc_sub(u, Ap);
+      const T ul = shfl_up1(AR::get(u));
+      if (out) {
+        // node (cx, cy): SW corner of cell (cx, cy), NW corner of cell (cx, cy - 1), plus the left lane
         Acc y = AR::zero();
-        AR::acc_add(y, sA[cNEn]);
-        AR::acc_add(y, sC[cNEn]);
-        AR::acc_add(y, sB[cNWn]);
-        AR::acc_sub(y, sC[cNWn]);
-        AR::acc_add(y, sC[cSWn]);
-        AR::acc_sub(y, sA[cSWn]);
-        AR::acc_sub(y, sB[cSEn]);
-        AR::acc_sub(y, sC[cSEn]);
-        const size_t s = (size_t)ix + (size_t)iy * m;
-        const T out = Epi<AR, TRS>::f(a.R, a.rlo, (size_t)(i - a.rbase) * a.Nx + s, AR::get(y));
-        Store<TYS>::put(a.Y, a.ylo, (size_t)(i - a.ybase) * a.Nx + s, out);
+        AR::acc_add(y, Ac);
+        AR::acc_add(y, Cc);
+        AR::acc_sub(y, Bp);
+        AR::acc_sub(y, Cp);
+        AR::acc_add(y, ul);
+        Store<TYS>::put(a.Y, a.ylo, yoff + s_node, E::f(rv, AR::get(y)));
       }
     }
-    __syncthreads();
+    Ap = Ac, Bp = Bc, Cp = Cc;
   }
 }
 
 template <class AR, typename TXS, typename TYS, typename TRS>
 int launch_t(sg_ctx* h, ApplyArgs& a) {
-  const int tiles_y = (h->m + OYN - 1) / OYN;
-  a.tiles_x = (h->m + OXN - 1) / OXN;
-  a.ngroups = (a.nrows + ROWS - 1) / ROWS;
-  const unsigned grid = (unsigned)a.ngroups * (unsigned)(a.tiles_x * tiles_y);
-  k_apply<AR, TXS, TYS, TRS><<<grid, NT, 0, h->stream>>>(a);
+  if (a.nrows > 65535) return sg_fail(h, SG_E_ARG, "apply: more than 65535 rows in one launch");
+  a.nwx = (h->m + 30) / 31;
+  a.nstrips = (h->m + a.strip - 1) / a.strip;
+  const unsigned gx = (unsigned)(((long)a.nwx * a.nstrips + WARPS - 1) / WARPS);
+  if (AR::kUsesTable && a.wdf)
+    k_apply<AR, true, TXS, TYS, TRS><<<dim3(gx, (unsigned)a.nrows), NT, 0, h->stream>>>(a);
+  else
+    k_apply<AR, false, TXS, TYS, TRS><<<dim3(gx, (unsigned)a.nrows), NT, 0, h->stream>>>(a);
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
   return SG_OK;
@@ -419,6 +464,8 @@ int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int
   a.row_ptr = T.row_ptr, a.tj = T.j, a.tk = T.k, a.g64 = T.g, a.g32 = T.gf, a.gdf = (const df2*)T.gdf;
   a.row0 = row0, a.nrows = nrows, a.ybase = ybase, a.rbase = rbase, a.n = h->n, a.m = h->m;
   a.Nx = h->Nx, a.Nc = h->Nc;
+  const int slot = arith == SG_F64 ? 0 : (arith == SG_DF64 ? 2 : 1);
+  a.strip = h->apply_strip[slot] > 0 ? h->apply_strip[slot] : STRIP_DEFAULT;
   if (arith == SG_F64) return pick_x<ArF64>(h, a, xprec, yprec, rprec);
   if (arith == SG_DF64) return pick_x<ArDF>(h, a, xprec, yprec, rprec);
   return pick_x<ArF32>(h, a, xprec, yprec, rprec);

@@ -14,6 +14,9 @@
 //            adds P x_{l+1}, post-smooths; reads b_l and x_{l+1}, writes x_l.
 //   mg_coarse one CTA per block runs every level with n_l <= 33 (down, coarsest
 //            solve, up) in shared memory.
+//   mg_down_tile / mg_up_tile  the same two level steps for the common case of a
+//            constant mean coefficient and V(1,1), as separable filters on
+//            shared-memory windows filled by cp.async (mg_tile.cuh).
 // Arithmetic type TA is double for SG_F64 and float otherwise; storage TS is
 // double, float or bf16 (bf16: FP32 accumulation, storage only).
 #include <algorithm>
@@ -22,7 +25,7 @@
 
 #include "sg_internal.h"
 #include "mg_kernels.cuh"
-#include "mg_c11.cuh"
+#include "mg_tile.cuh"
 
 namespace {
 constexpr int NC0 = 33;                                  // levels with n <= NC0 run in mg_coarse
@@ -151,13 +154,9 @@ template <typename TB, typename TS, typename TA>
 int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1) {
-    // strip height: as tall as possible while still giving every SM ~24 warps
-    int srows = SLIDE_ROWS;
-    const int sx = (C.m + 31) / 32;
-    while (srows > 2 && (long)sx * ((C.m + srows - 1) / srows) * nb < 152L * 24) srows /= 2;
-    const int ns = sx * ((C.m + srows - 1) / srows);
-    mg_down_slide<TB, TS, TA><<<dim3((ns + SLIDE_WARPS - 1) / SLIDE_WARPS, nb), 32 * SLIDE_WARPS, 0, h->stream>>>(
-        b, bc, F.m, C.m, F.N, C.N, (TA)(h->omega * 3.0 / 8.0), sx, ns, srows);
+    const int tx = (C.m + MD_TX - 1) / MD_TX, ty = (C.m + MD_TY - 1) / MD_TY;
+    mg_down_tile<TB, TS, TA><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, bc, F.m, C.m, F.N, C.N,
+                                                                            (TA)(h->omega * 3.0 / 8.0), tx);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;
@@ -178,12 +177,9 @@ template <typename TB, typename TS, typename TA>
 int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TS* x) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1 && h->nu2 == 1) {
-    int srows = SLIDE_ROWS;
-    const int sx = (F.m + 63) / 64;
-    while (srows > 2 && (long)sx * ((F.m + 2 * srows - 1) / (2 * srows)) * nb < 152L * 24) srows /= 2;
-    const int ns = sx * ((F.m + 2 * srows - 1) / (2 * srows));
-    mg_up_slide<TB, TS, TA><<<dim3((ns + SLIDE_WARPS - 1) / SLIDE_WARPS, nb), 32 * SLIDE_WARPS, 0, h->stream>>>(
-        b, xc, x, F.m, C.m, F.N, C.N, F.N, (TA)(h->omega * 3.0 / 8.0), sx, ns, srows);
+    const int tx = (F.m + MU_FX - 1) / MU_FX, ty = (F.m + MU_FY - 1) / MU_FY;
+    mg_up_tile<TB, TS, TA><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N,
+                                                                          (TA)(h->omega * 3.0 / 8.0), tx);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;

@@ -166,14 +166,6 @@ __global__ void __launch_bounds__(NT) k_axpys_df(const float* __restrict__ V, si
   reduce_out<1>(acc, partial, out, counter, 1);
 }
 
-__global__ void k_scale_df(float* __restrict__ v, size_t N, df2 sc) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    const df2 r = df_mul(ldf(v, N, i), sc);
-    v[i] = r.hi;
-    v[i + N] = r.lo;
-  }
-}
-
 template <typename TZ, int NV>
 __global__ void k_update_df(float* __restrict__ U, const TZ* __restrict__ Z, size_t ldz, int nz,
                             const double* __restrict__ y, size_t N, size_t lo) {
@@ -204,11 +196,6 @@ __global__ void k_df_from_f64(const double* __restrict__ x, float* __restrict__ 
 __global__ void k_df_to_f64(const float* __restrict__ x, double* __restrict__ y, size_t N, size_t lo) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i] + (double)x[i + lo];
-}
-
-__global__ void k_scale(const double* __restrict__ w, double* __restrict__ v, size_t N, double s) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
-    v[i] = w[i] * s;
 }
 
 template <typename TZ, int NV>
@@ -425,13 +412,6 @@ int df_axpys_norm(sg_ctx* h, const float* V, size_t ldv, int nv, const double* h
   return SG_OK;
 }
 
-int df_scale(sg_ctx* h, float* v, size_t N, double s) {
-  k_scale_df<<<grid_for(N), 256, 0, h->stream>>>(v, N, df_from_double(s));
-  SG_CUDA(h, cudaGetLastError());
-  count_launch(h);
-  return SG_OK;
-}
-
 int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t ldz, int nz, const double* y_host,
               size_t N) {
   int rc = ensure_reduction(h);
@@ -470,18 +450,21 @@ int df_to_f64(sg_ctx* h, const float* x, double* y, size_t N, size_t lo) {
 }
 
 // copy count results of reduction slot (0 dots, 1 axpys norm, 3 dot pairs) to the host
+int upload_red(sg_ctx* h, int slot, const double* host, int count) {
+  if (count > MAXOUT) return sg_fail(h, SG_E_ARG, "reduction slot overflow");
+  std::copy(host, host + count, h->red_host + slot * MAXOUT);
+  SG_CUDA(h, cudaMemcpyAsync(h->red_out + slot * MAXOUT, h->red_host + slot * MAXOUT, sizeof(double) * count,
+                             cudaMemcpyHostToDevice, h->stream));
+  return SG_OK;
+}
+
+const double* red_slot(const sg_ctx* h, int slot) { return h->red_out + slot * MAXOUT; }
+
 int copy_red(sg_ctx* h, int slot, int count, double* out_host) {
   SG_CUDA(h, cudaMemcpyAsync(h->red_host + slot * MAXOUT, h->red_out + slot * MAXOUT, sizeof(double) * count,
                              cudaMemcpyDeviceToHost, h->stream));
   SG_CUDA(h, cudaStreamSynchronize(h->stream));
   std::copy(h->red_host + slot * MAXOUT, h->red_host + slot * MAXOUT + count, out_host);
-  return SG_OK;
-}
-
-int vec_scale(sg_ctx* h, const double* w, double* v, size_t N, double s) {
-  k_scale<<<grid_for(N), 256, 0, h->stream>>>(w, v, N, s);
-  SG_CUDA(h, cudaGetLastError());
-  count_launch(h);
   return SG_OK;
 }
 

@@ -1,0 +1,219 @@
+// Constant-coefficient V(1,1) level kernels, shared-memory tiled (included by k_mg.cu
+// after mg_kernels.cuh).
+//
+// With c = omega / (8/3) and A = 3 I - S9/3 (S9 = 3 x 3 box sum) the fused level
+// operations are separable filters:
+//   down:  b_c = P^T (b - A c b) = (1 - 3c) (r3 (x) r3) b + (c/3) (r5 (x) r5) b,
+//          r3 = (1/2, 1, 1/2), r5 = r3 * (1,1,1) = (1/2, 3/2, 2, 3/2, 1/2), centred on the
+//          fine node 2I+1 that carries coarse node I;
+//   up:    x = c b + e (e = P x_c) followed by one Jacobi step:
+//          x' = (2c - 3c^2) b + (1 - 3c) e + S9 g,   g = (c^2/3) b + (c/3) e.
+// A CTA first copies the window of the fine (and coarse) grid its tile needs into shared
+// memory with 16-byte cp.async copies -- many bytes in flight per SM, which is what a
+// streaming stencil needs to run at HBM speed -- and then evaluates the filters from
+// shared memory, each warp walking a few rows with the partial sums in registers.
+// Level arrays have an odd row length, so rows are not 16-byte aligned: the loader
+// copies the aligned middle of every row segment asynchronously and the ragged ends with
+// plain loads, and never reads outside the array.
+#pragma once
+#include <cstdint>
+
+namespace {
+constexpr int MT_THREADS = 256;
+constexpr int MD_TX = 64, MD_TY = 16;     // down: coarse tile (columns x rows)
+constexpr int MU_FX = 128, MU_FY = 32;    // up: fine tile (columns x rows)
+
+template <typename T> __device__ __forceinline__ T zero_of() { return T(0); }
+template <> __device__ __forceinline__ bf16 zero_of<bf16>() { return __float2bfloat16_rn(0.f); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Shared-memory row pitch (elements) for a window NC columns wide: room for the
+// alignment phase (< 16 bytes) and a multiple of 16 bytes.
+template <typename T, int NC> constexpr int win_pitch() {
+  constexpr int V = 16 / (int)sizeof(T);
+  return ((NC + 2 * V - 2) / V) * V;
+}
+
+// Copies rows [r0, r0 + NR) x columns [c0, c0 + NC) of the m x m array g into sw (row rr at
+// sw + rr * SW + sph[rr]), with zeros outside the array.  Call with all MT_THREADS threads,
+// then cp_async_wait_all() and __syncthreads() before reading.  Each warp takes rows
+// warp, warp + 8, ...: the 16-byte aligned middle of a row goes by cp.async, the up to
+// 2 (V - 1) ragged end elements by plain loads that are all issued before any of them is
+// stored, so a warp waits for one memory latency, not one per row.
+template <typename T, int NR, int NC>
+__device__ __forceinline__ void load_window(const T* __restrict__ g, int m, int r0, int c0, T* sw, int* sph) {
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int SW = win_pitch<T, NC>();
+  constexpr int NW = MT_THREADS / 32;
+  constexpr int RPW = (NR + NW - 1) / NW;               // rows per warp
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T endv[RPW];
+  int endk[RPW];                                        // window column of this lane's end element, or -1
+#pragma unroll
+  for (int q = 0; q < RPW; ++q) {
+    const int rr = warp + q * NW;
+    endk[q] = -1;
+    endv[q] = zero_of<T>();
+    if (rr >= NR) continue;
+    const int r = r0 + rr;
+    if (r < 0 || r >= m) {
+      if (lane == 0) sph[rr] = 0;
+      continue;
+    }
+    const T* grow = g + (size_t)r * m;
+    const uintptr_t a0 = (uintptr_t)grow + (uintptr_t)((intptr_t)c0 * (intptr_t)sizeof(T));
+    const int ph = (int)((a0 & 15u) / sizeof(T));
+    if (lane == 0) sph[rr] = ph;
+    T* sbase = sw + rr * SW + ph;                       // column c0 + k lands at sbase[k]
+    const int cl = max(c0, 0), cr = min(c0 + NC, m);
+    const int ca = cl + (V - (cl - c0 + ph) % V) % V;   // first 16-byte aligned column >= cl
+    const int nch = cr > ca ? (cr - ca) / V : 0;
+    const int cb = ca + nch * V;
+    for (int qq = lane; qq < nch; qq += 32) cp_async16(sbase + (ca - c0) + qq * V, grow + ca + qq * V);
+    // ragged ends: [cl, min(ca, cr)) and [max(cb, ca), cr), at most V - 1 columns each
+    const int nh = min(ca, cr) - cl, t0 = max(cb, ca), ntl = cr - t0;
+    int c = -1;
+    if (lane < V - 1) c = lane < nh ? cl + lane : -1;
+    else if (lane < 2 * (V - 1)) c = lane - (V - 1) < ntl ? t0 + lane - (V - 1) : -1;
+    if (c >= 0) {
+      endv[q] = grow[c];
+      endk[q] = c - c0;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPW; ++q) {
+    const int rr = warp + q * NW;
+    if (rr >= NR) continue;
+    const int r = r0 + rr;
+    T* srow = sw + rr * SW;
+    if (r < 0 || r >= m) {
+      for (int k = lane; k < NC; k += 32) srow[k] = zero_of<T>();
+      continue;
+    }
+    const uintptr_t a0 = (uintptr_t)(g + (size_t)r * m) + (uintptr_t)((intptr_t)c0 * (intptr_t)sizeof(T));
+    T* sbase = srow + (int)((a0 & 15u) / sizeof(T));
+    if (endk[q] >= 0) sbase[endk[q]] = endv[q];
+    // zeros left and right of the grid
+    const int zl = max(0, min(NC, -c0)), zr = max(0, min(NC, c0 + NC - m));
+    for (int k = lane; k < zl; k += 32) sbase[k] = zero_of<T>();
+    for (int k = lane; k < zr; k += 32) sbase[NC - 1 - k] = zero_of<T>();
+  }
+}
+
+template <typename TA, typename T> __device__ __forceinline__ TA sld(const T* p) { return ld_as<TA>(p); }
+
+// ---------------------------------------------------------------------------
+// down: tile of MD_TX x MD_TY coarse nodes; fine window rows 2J0-1 .. 2J0+2MD_TY+1,
+// columns 2I0-1 .. 2I0+2MD_TX+1.  Warp w: coarse columns 32 (w & 1) + lane, coarse rows
+// 4 (w >> 1) .. +3.
+template <typename TB, typename TS, typename TA>
+__global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict__ b, TS* __restrict__ bc, int m,
+                                                           int mc, size_t ldb, size_t ldc, TA c, int tiles_x) {
+  constexpr int NR = 2 * MD_TY + 3, NC = 2 * MD_TX + 3, SW = win_pitch<TB, NC>();
+  __shared__ __align__(16) TB sw[NR * SW];
+  __shared__ int sph[NR];
+  const int I0 = (blockIdx.x % tiles_x) * MD_TX, J0 = (blockIdx.x / tiles_x) * MD_TY;
+  load_window<TB, NR, NC>(b + (size_t)blockIdx.y * ldb, m, 2 * J0 - 1, 2 * I0 - 1, sw, sph);
+  cp_async_wait_all();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;           // coarse column within the tile
+  const int jw = 4 * (warp >> 1);                 // first coarse row of this warp
+  const int I = I0 + i;
+  const TA a3 = TA(1) - TA(3) * c, a5 = c / TA(3);
+  TA h3[11], h5[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+    const int rr = 2 * jw + k;
+    const TB* row = sw + rr * SW + sph[rr] + 2 * i;     // window columns 2i .. 2i+4
+    const TA x0 = sld<TA>(row), x1 = sld<TA>(row + 1), x2 = sld<TA>(row + 2), x3 = sld<TA>(row + 3),
+             x4 = sld<TA>(row + 4);
+    h3[k] = TA(0.5) * (x1 + x3) + x2;
+    h5[k] = TA(0.5) * (x0 + x4) + TA(1.5) * (x1 + x3) + TA(2) * x2;
+  }
+  TS* cb = bc + (size_t)blockIdx.y * ldc;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int J = J0 + jw + q;
+    const TA v3 = TA(0.5) * (h3[2 * q + 1] + h3[2 * q + 3]) + h3[2 * q + 2];
+    const TA v5 = TA(0.5) * (h5[2 * q] + h5[2 * q + 4]) + TA(1.5) * (h5[2 * q + 1] + h5[2 * q + 3]) + TA(2) * h5[2 * q + 2];
+    if (I < mc && J < mc) st_as<TS, TA>(cb + (size_t)J * mc + I, a3 * v3 + a5 * v5);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// up: tile of MU_FX x MU_FY fine nodes starting at (X0, Y0) (both even).  b window: fine
+// rows Y0-1 .. Y0+MU_FY, columns X0-1 .. X0+MU_FX; x_c window: coarse rows Y0/2-1 ..
+// Y0/2+MU_FY/2, columns X0/2-1 .. X0/2+MU_FX/2.  Fine node i lies between coarse nodes
+// (i-1)>>1 and i>>1 (the same node for odd i).  Warp w: fine columns X0 + 64 (w & 1) +
+// 2 lane + {0, 1}, fine rows Y0 + 8 (w >> 1) .. +7.
+template <typename TB, typename TS, typename TA>
+__global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ b, const TS* __restrict__ xc,
+                                                         TS* __restrict__ x, int m, int mc, size_t ldb, size_t ldc,
+                                                         size_t ldx, TA c, int tiles_x) {
+  constexpr int NRB = MU_FY + 2, NCB = MU_FX + 2, SWB = win_pitch<TB, NCB>();
+  constexpr int NRC = MU_FY / 2 + 2, NCC = MU_FX / 2 + 2, SWC = win_pitch<TS, NCC>();
+  __shared__ __align__(16) TB sb[NRB * SWB];
+  __shared__ __align__(16) TS sc[NRC * SWC];
+  __shared__ int phb[NRB], phc[NRC];
+  const int X0 = (blockIdx.x % tiles_x) * MU_FX, Y0 = (blockIdx.x / tiles_x) * MU_FY;
+  load_window<TB, NRB, NCB>(b + (size_t)blockIdx.y * ldb, m, Y0 - 1, X0 - 1, sb, phb);
+  load_window<TS, NRC, NCC>(xc + (size_t)blockIdx.y * ldc, mc, Y0 / 2 - 1, X0 / 2 - 1, sc, phc);
+  cp_async_wait_all();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k0 = 64 * (warp & 1) + 2 * lane;      // fine column offset of i0 within the tile
+  const int i0 = X0 + k0, i1 = i0 + 1;
+  const int jw = 8 * (warp >> 1);                 // first fine row offset of this warp
+  const TA cgb = c * c / TA(3), cge = c / TA(3), cbb = TA(2) * c - TA(3) * c * c, cee = TA(1) - TA(3) * c;
+  // coarse window column of coarse node C = X0/2 + k0/2 (the node under i1) is k0/2 + 1
+  const int cc = k0 / 2 + 1;
+  const bool okm = i0 - 1 >= 0 && i0 - 1 < m, ok0 = i0 < m, ok1 = i1 < m, okp = i1 + 1 < m;
+  TA H0[10], H1[10], be0[8], be1[8];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const int jr = jw + k - 1;                    // fine row offset from Y0 (-1 .. 32)
+    const int j = Y0 + jr;
+    const bool jok = j >= 0 && j < m;
+    // coarse rows under fine row j: lo = (j-1)>>1, hi = j>>1 (window rows + 1 - Y0/2)
+    const int rlo = ((jr - 1) >> 1) + 1, rhi = (jr >> 1) + 1;
+    const TA wa = (j & 1) ? TA(1) : TA(0.5), wb = (j & 1) ? TA(0) : TA(0.5);
+    const TS* clo = sc + rlo * SWC + phc[rlo] + cc;
+    const TS* chi = sc + rhi * SWC + phc[rhi] + cc;
+    const TA em1 = wa * sld<TA>(clo - 1) + wb * sld<TA>(chi - 1);   // coarse C-1 at row j
+    const TA e_c = wa * sld<TA>(clo) + wb * sld<TA>(chi);           // coarse C
+    const TA ep1 = wa * sld<TA>(clo + 1) + wb * sld<TA>(chi + 1);   // coarse C+1
+    // prolongation to the four fine columns i0-1 (odd, on C-1), i0 (even), i1 (odd, on C), i1+1
+    const TA e_m = em1, e_0 = TA(0.5) * (em1 + e_c), e_1 = e_c, e_p = TA(0.5) * (e_c + ep1);
+    const TB* brow = sb + (jr + 1) * SWB + phb[jr + 1] + k0;         // window column of i0 - 1
+    const TA b_m = sld<TA>(brow), b_0 = sld<TA>(brow + 1), b_1 = sld<TA>(brow + 2), b_p = sld<TA>(brow + 3);
+    const TA g_m = jok && okm ? cgb * b_m + cge * e_m : TA(0);
+    const TA g_0 = jok && ok0 ? cgb * b_0 + cge * e_0 : TA(0);
+    const TA g_1 = jok && ok1 ? cgb * b_1 + cge * e_1 : TA(0);
+    const TA g_p = jok && okp ? cgb * b_p + cge * e_p : TA(0);
+    H0[k] = (g_m + g_0) + g_1;
+    H1[k] = (g_0 + g_1) + g_p;
+    if (k >= 1 && k <= 8) {
+      be0[k - 1] = cbb * b_0 + cee * e_0;
+      be1[k - 1] = cbb * b_1 + cee * e_1;
+    }
+  }
+  TS* xb = x + (size_t)blockIdx.y * ldx;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = Y0 + jw + q;
+    if (j < m) {
+      TS* op = xb + (size_t)j * m;
+      if (ok0) st_as<TS, TA>(op + i0, be0[q] + ((H0[q] + H0[q + 1]) + H0[q + 2]));
+      if (ok1) st_as<TS, TA>(op + i1, be1[q] + ((H1[q] + H1[q + 1]) + H1[q + 2]));
+    }
+  }
+}
+}  // namespace

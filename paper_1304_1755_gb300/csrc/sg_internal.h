@@ -99,6 +99,7 @@ struct sg_ctx {
   int red_blocks = 0;
   double* kv = nullptr;                 // (restart + 1) FP64 vectors
   int kv_cap = 0;
+  int kv_layout = -1;                   // 0: FP64 basis vectors, 1: double-float (what the padding holds)
   void* kz = nullptr;                   // restart vectors in pc precision
   int kz_cap = 0, kz_prec = -1;
   double* ktmp = nullptr;               // 4 FP64 work vectors
@@ -106,6 +107,7 @@ struct sg_ctx {
   Tracer tr;
   int phase = 3;
   bool true_res_valid = false;          // the solver already computed the final FP64 true residual
+  int apply_strip[3] = {0, 0, 0};       // operator kernel strip height per arithmetic (FP64, FP32, DF); 0 = default
   // CUDA graphs of whole preconditioner applications, keyed by their operands
   struct GraphEntry {
     cudaGraphExec_t exec;
@@ -188,7 +190,6 @@ int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
 int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host);
 int vec_axpys_norm(sg_ctx* h, const double* V, size_t ldv, int nv, const double* hcoef_dev, double* w, size_t N,
                    double* nrm2_host);
-int vec_scale(sg_ctx* h, const double* w, double* v, size_t N, double s);
 int vec_update(sg_ctx* h, double* U, int zprec, const void* Z, size_t ldz, int nz, const double* y_host, size_t N);
 int vec_cast(sg_ctx* h, int iprec, const void* in, int oprec, void* out, size_t N);
 int vec_axpby(sg_ctx* h, double a, const double* x, double b, double* y, size_t N);   // y = a x + b y
@@ -197,12 +198,14 @@ int vec_dot_pairs(sg_ctx* h, int npairs, const double* const* xs, const void* co
 int vec_axpy_prec(sg_ctx* h, double a, int xprec, const void* x, double* y, size_t N);  // y += a x
 int ensure_reduction(sg_ctx* h);
 int copy_red(sg_ctx* h, int slot, int count, double* out_host);
+// host -> reduction slot (device), stream-ordered; slot 3 carries Gram-Schmidt coefficients
+int upload_red(sg_ctx* h, int slot, const double* host, int count);
+const double* red_slot(const sg_ctx* h, int slot);
 // Double-float Krylov vectors: hi[0..Np), lo[Np..2Np) with the padded length Np (a multiple
 // of 64, padding kept at zero); dots/axpys/scale take Np, the others the true length N
 // and the lo offset.
 int df_dots(sg_ctx* h, const float* V, size_t ldv, int nv, const float* w, size_t Np, bool with_ww);   // red slot 0
 int df_axpys_norm(sg_ctx* h, const float* V, size_t ldv, int nv, const double* hc_dev, float* w, size_t Np);  // slot 1
-int df_scale(sg_ctx* h, float* v, size_t Np, double s);
 int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t ldz, int nz, const double* y_host,
               size_t N);
 int df_from_f64(sg_ctx* h, const double* x, float* y, size_t N, size_t lo);

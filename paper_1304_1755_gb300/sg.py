@@ -69,6 +69,9 @@ SIGNATURES = {
     "sg_vcycle": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_vcycle_static": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_solve": (ctypes.c_int, [VP, VP, VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
+    "sg_solve_batch": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_int,
+                                      ctypes.POINTER(SolveOpts), VP, ctypes.c_int]),
+    "sg_autotune": (ctypes.c_int, [VP, ctypes.c_int]),
     "sg_objective": (ctypes.c_int, [VP, VP, DP, VP]),
     "sg_adjoint_gradients": (ctypes.c_int, [VP, VP, VP, ctypes.c_double, VP, DP]),
     "sg_timing_enable": (ctypes.c_int, [VP, ctypes.c_int]),
@@ -187,6 +190,10 @@ class Handle:
             _check(rc, self.h)
         return info
 
+    def autotune(self, which=0):
+        """sg_autotune: time the operator kernel's tile candidates for this problem and keep the best."""
+        _check(lib().sg_autotune(self.h, which), self.h)
+
     def objective(self, U, G=None):
         J = ctypes.c_double()
         _check(lib().sg_objective(self.h, _ptr(U), ctypes.byref(J), _ptr(G)), self.h)
@@ -206,3 +213,23 @@ class Handle:
         gs = ctypes.c_double()
         _check(lib().sg_adjoint_gradients(self.h, _ptr(U), _ptr(Lam), sigma, _ptr(g_abar), ctypes.byref(gs)), self.h)
         return gs.value
+
+
+def solve_batch(handles, Fs, Us, nstreams=8, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8,
+                pc_prec=F64, transpose=False, reorth=0, arith=ARITH_F64, check=True):
+    """sg_solve_batch: solve independent systems (one Handle each) concurrently on nstreams
+    streams; returns one SolveInfo per system (status = that system's sg_solve result)."""
+    n = len(handles)
+    if len(Fs) != n or len(Us) != n:
+        raise ValueError("handles, Fs and Us must have the same length")
+    o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, reorth, arith)
+    hs = (VP * n)(*[h.h for h in handles])
+    fp = (VP * n)(*[_ptr(F) for F in Fs])
+    up = (VP * n)(*[_ptr(U) for U in Us])
+    infos = (SolveInfo * n)()
+    rc = lib().sg_solve_batch(hs, fp, up, n, ctypes.byref(o), ctypes.cast(infos, VP), nstreams)
+    if check and rc != 0:
+        bad = [i for i in range(n) if infos[i].status != 0]
+        raise SGError(rc, f"sg_solve_batch: systems {bad} failed" + (
+            f": {lib().sg_last_error(handles[bad[0]].h).decode()}" if bad else ""))
+    return list(infos)

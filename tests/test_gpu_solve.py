@@ -157,3 +157,21 @@ def test_nonfinite_rhs_reported():
     U = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
     info = pr.h.solve(dev(F), U, check=False)
     assert info.status == -6
+
+
+def test_switching_krylov_arithmetic_on_one_handle():
+    """Double-float and FP64 solves alternate on one handle (they share the Krylov workspace,
+    whose padding each layout needs zeroed): every solve converges to the same solution."""
+    import torch
+    pr = Pair(65, 3, 3, sigma=0.3)
+    F = dev(osg.rhs(pr.sys))
+    Ustar = _direct(pr, host(F))
+    df = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=20, tol=1e-10, pc_prec=sg.F32, arith=sg.ARITH_DF64)
+    f64 = dict(df, pc_prec=sg.F64, arith=sg.ARITH_F64)
+    for opts in (df, f64, df, f64, df):
+        U = torch.zeros_like(F)
+        info = pr.h.solve(F, U, **opts)
+        torch.cuda.synchronize()
+        assert info.status == 0 and info.relres_true <= 1e-10
+        got = host(U)
+        assert np.linalg.norm(got - Ustar) <= 1e-6 * np.linalg.norm(Ustar)
