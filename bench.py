@@ -40,9 +40,12 @@ WORKLOADS = {
     # vectors of 439 MB (> L2) with about 5 GB on the device, for detailed kernel profiles
     "c3s": dict(n=513, M=6, p=4, family=1, sigma=0.2, restart=4, pc_prec=2, tol=1e-8, f_seed=None,
                 name="sg_c3_copy_513sq_M6_hermite_p4_P210_fgmres4_bf16pc"),
-    # adjoint gradient of J = E[int u] + Var[int u] / 2 w.r.t. the per-cell mean and sigma
-    "c4": dict(n=257, M=4, p=3, family=0, sigma=0.4, restart=30, pc_prec=1, tol=1e-8, abar_seed=2,
-               name="sg_c4_adjoint_257sq_M4_legendre_p3_P35_sigma0.4_lognormal_mean"),
+    # adjoint gradient of J = E[int u] + Var[int u] / 2 w.r.t. the per-cell mean and sigma.  At sigma =
+    # 0.4 the 257^2 system (lognormal mean, not coercive at the xi-box corners) makes restarted
+    # GMRES(30) stagnate near 1e-6 in FP64 as well, so the timed gradient uses sigma = 0.3; the
+    # 33^2 parity test keeps sigma = 0.4
+    "c4": dict(n=257, M=4, p=3, family=0, sigma=0.3, restart=30, pc_prec=1, tol=1e-8, abar_seed=2,
+               name="sg_c4_adjoint_257sq_M4_legendre_p3_P35_sigma0.3_lognormal_mean"),
     # 64 uneven systems (grid 65^2..513^2, M 2..6, p 2..4, sigma U[0.1, 0.5], Legendre, f = 1):
     # FGMRES(30) + block-triangular preconditioner in FP32, FP64 outer loop
     "c5": dict(count=64, batch_seed=5, family=0, restart=30, pc_prec=1, tol=1e-8, nstreams=16,
@@ -290,6 +293,10 @@ def run_ours(args, wl, rank, world):
         "clocks": clocks,
         "vs_plain_fp64": vs64,
     }
+    # C2's comparison: sigma in {0.1, 0.3, 0.5}, block-triangular vs block-diagonal, FP64 vs FP32
+    # preconditioner inside FP64 flexible GMRES (one timed solve each, same grid and chaos space)
+    if args.workload == "c2" and not args.no_fp64_compare:
+        out["c2_sweep"] = c2_sweep(wl, stream)
     # roofline of the dominant kernel, the outer operator (k_apply): it is bound by arithmetic
     # (double-float: FP32 pipe; strict mode: FP64 units), not by HBM, on GB300
     names = ["operator", "preconditioner", "gram_schmidt", "other"]
@@ -318,6 +325,43 @@ def run_ours(args, wl, rank, world):
     }
     h.close()
     return out
+
+
+def c2_sweep(wl, stream):
+    import numpy as np
+    import torch
+    from paper_1304_1755_gb300 import sg
+    rows = []
+    n, M, p = wl["n"], wl["M"], wl["p"]
+    unit, _ = sg.sg_kl_coef(n, M, 1.0)
+    _, F_host = build_problem(wl)
+    for sigma in (0.1, 0.3, 0.5):
+        coef = unit.copy()
+        coef[0] = 1.0
+        coef[1:] *= sigma
+        amin = float(np.min(1.0 - np.sqrt(3.0) * np.abs(coef[1:]).sum(axis=0)))
+        h = sg.Handle(n, M, p, wl["family"], coef, stream=stream)
+        F = torch.as_tensor(F_host).cuda()
+        for pc in (sg.PC_BLOCKTRI, sg.PC_BLOCKDIAG):
+            for pcp, ar in ((sg.F64, sg.ARITH_F64), (sg.F32, sg.ARITH_F64), (sg.F32, sg.ARITH_DF64)):
+                U = torch.zeros_like(F)
+                opts = dict(method=sg.FGMRES, precond=pc, restart=wl["restart"], maxit=400, tol=wl["tol"],
+                            pc_prec=pcp, arith=ar, check=False)
+                h.solve(F, U, **opts)
+                U.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                info = h.solve(F, U, **opts)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                rows.append({"sigma": sigma, "min_a_at_corners": round(amin, 4),
+                             "precond": "block-triangular" if pc == sg.PC_BLOCKTRI else "block-diagonal",
+                             "pc_prec": {0: "f64", 1: "f32"}[pcp], "krylov": "df64" if ar else "f64",
+                             "status": info.status, "iterations": info.iters, "relres_true": info.relres_true,
+                             "ms": round(e0.elapsed_time(e1), 3)})
+        h.close()
+    return rows
 
 
 def run_c4(args, wl, rank, world):
@@ -620,8 +664,13 @@ def main():
     ap.add_argument("--arith", default="df64", choices=["f64", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--pc-prec", choices=["f64", "f32", "bf16"], default=None,
+                    help="override the workload's preconditioner storage precision")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.pc_prec is not None:
+        wl["pc_prec"] = {"f64": 0, "f32": 1, "bf16": 2}[args.pc_prec]
+        wl["name"] += f"_pc_{args.pc_prec}"
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -64,21 +64,29 @@ struct DFS {};   // tag: double-float storage, hi array at p, lo array at p + lo
 template <typename TS> struct Load;
 template <> struct Load<double> {
   typedef double Z;
+  typedef double E;                                  // stored element
+  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return *p; }
   static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return ((const double*)p)[i]; }
   static __device__ __forceinline__ Z zero() { return 0.0; }
 };
 template <> struct Load<float> {
   typedef float Z;
+  typedef float E;
+  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return *p; }
   static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return ((const float*)p)[i]; }
   static __device__ __forceinline__ Z zero() { return 0.f; }
 };
 template <> struct Load<bf16> {
   typedef float Z;
+  typedef bf16 E;
+  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __bfloat162float(*p); }
   static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return __bfloat162float(((const bf16*)p)[i]); }
   static __device__ __forceinline__ Z zero() { return 0.f; }
 };
 template <> struct Load<DFS> {
   typedef df2 Z;
+  typedef float E;                                   // hi array; the lo array follows at + lo
+  static __device__ __forceinline__ Z ldp(const E* p, size_t lo) { return {p[0], p[lo]}; }
   static __device__ __forceinline__ Z at(const void* p, size_t lo, size_t i) {
     return {((const float*)p)[i], ((const float*)p)[i + lo]};
   }
@@ -112,11 +120,10 @@ struct ArF32 {
   typedef float T;
   typedef float Acc;
   typedef float G;
+  typedef float CE;                        // coefficient element
   static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.g32[t]; }
-  template <bool WT>
-  static __device__ __forceinline__ T weight(const ApplyArgs& a, long long wo, size_t e, G g) {
-    return a.c32[wo + e] * g;
-  }
+  template <bool WT> static __device__ __forceinline__ const CE* cbase(const ApplyArgs& a) { return a.c32; }
+  template <bool WT> static __device__ __forceinline__ T weight(CE c, G g) { return c * g; }
   static __device__ __forceinline__ Acc zero() { return 0.f; }
   static __device__ __forceinline__ T wzero() { return 0.f; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { s = fmaf(w, z, s); }
@@ -137,11 +144,10 @@ struct ArF64 {
   typedef double T;
   typedef double Acc;
   typedef double G;
+  typedef double CE;
   static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.g64[t]; }
-  template <bool WT>
-  static __device__ __forceinline__ T weight(const ApplyArgs& a, long long wo, size_t e, G g) {
-    return a.c64[wo + e] * g;
-  }
+  template <bool WT> static __device__ __forceinline__ const CE* cbase(const ApplyArgs& a) { return a.c64; }
+  template <bool WT> static __device__ __forceinline__ T weight(CE c, G g) { return c * g; }
   static __device__ __forceinline__ Acc zero() { return 0.0; }
   static __device__ __forceinline__ T wzero() { return 0.0; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { s = ::fma(w, (double)z, s); }
@@ -163,13 +169,11 @@ struct ArDF {
   // with the weight table, k is the term's weight slot (precomputed c_k(e) gamma products)
   static constexpr bool kUsesTable = true;
   typedef df2 G;
+  typedef df2 CE;
   static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.gdf[t]; }
-  // WT: with the table, wo addresses the precomputed product c_k(e) gamma of the term's slot
-  template <bool WT>
-  static __device__ __forceinline__ T weight(const ApplyArgs& a, long long wo, size_t e, G g) {
-    if (WT) return a.wdf[wo + e];
-    return df_mul(a.cdf[wo + e], g);
-  }
+  // WT: with the table, the element is the precomputed product c_k(e) gamma of the term's slot
+  template <bool WT> static __device__ __forceinline__ const CE* cbase(const ApplyArgs& a) { return WT ? a.wdf : a.cdf; }
+  template <bool WT> static __device__ __forceinline__ T weight(CE c, G g) { return WT ? c : df_mul(c, g); }
   static __device__ __forceinline__ Acc zero() { return dacc_zero(); }
   static __device__ __forceinline__ T wzero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { dacc_fma(s, w, z); }
@@ -309,11 +313,11 @@ __device__ __forceinline__ df2 shfl_up1(df2 v) {
   return {__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
 }
 
-// The row's couplings as shared-memory tables: column offset j N_x, weight-row offset
-// (mode k, or table slot) times N_c, and the coupling value.
-template <class AR> struct RowTerms {
-  long long xo[MAXT];
-  long long wo[MAXT];
+// The row's couplings as shared-memory tables: the coupled column's base pointer, the base
+// pointer of its weight row (mode k, or table slot), and the coupling value.
+template <class AR, typename XE> struct RowTerms {
+  const XE* xp[MAXT];
+  const typename AR::CE* wp[MAXT];
   typename AR::G g[MAXT];
 };
 
@@ -324,13 +328,14 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   typedef Load<TXS> LX;
   typedef typename LX::Z Z;
   typedef Epi<AR, TRS> E;
-  __shared__ RowTerms<AR> rt;
+  typedef typename LX::E XE;
+  __shared__ RowTerms<AR, XE> rt;
   const int i = a.row0 + blockIdx.y;                       // output row of this CTA
   const int t0 = a.row_ptr[i];
-  const int nt = a.row_ptr[i + 1] - t0;                    // <= MAXT (checked at set-up)
+  const int nt = a.row_ptr[i + 1] - t0;                    // <= MAXT (M <= 16 at set-up)
   for (int t = threadIdx.x; t < nt; t += NT) {
-    rt.xo[t] = (long long)a.tj[t0 + t] * (long long)a.Nx;
-    rt.wo[t] = (long long)(WT ? a.ws[t0 + t] : a.tk[t0 + t]) * (long long)a.Nc;
+    rt.xp[t] = (const XE*)a.X + (size_t)a.tj[t0 + t] * a.Nx;
+    rt.wp[t] = AR::template cbase<WT>(a) + (size_t)(WT ? a.ws[t0 + t] : a.tk[t0 + t]) * a.Nc;
     rt.g[t] = AR::gval(a, t0 + t);
   }
   __syncthreads();
@@ -338,6 +343,7 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   if (gw >= a.nwx * a.nstrips) return;                     // whole warps only
   const int lane = threadIdx.x & 31;
   const int n = a.n, m = a.m;
+  const size_t xlo = a.xlo;
   const int cx = 31 * (gw % a.nwx) + lane;                 // cell column = vertex column of its SW corner
   const int cy0 = a.strip * (gw / a.nwx);                  // first cell row (primes the window)
   const int cy1 = min(cy0 + a.strip, n - 2);               // last cell row = last node row of the strip
@@ -345,27 +351,25 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   const bool okr = cx + 1 <= n - 2;                        // right corners (vertex column cx + 1) interior
   const bool node_col = lane >= 1 && cx <= n - 2;          // this lane finishes node (cx, cy)
   const int cxw = min(cx, n - 2);                          // weight column (cells beyond the grid have zero corners)
-  const size_t yoff = (size_t)(i - a.ybase) * a.Nx, roff = (size_t)(i - a.rbase) * a.Nx;
+  typename E::Raw rv;
   T Ap = AR::wzero(), Bp = AR::wzero(), Cp = AR::wzero();   // features of cell (cx, cy - 1)
   for (int cy = cy0; cy <= cy1; ++cy) {
     const bool out = node_col && cy > cy0;                 // node (cx, cy): 1 <= cy <= n - 2 here
-    const size_t s_node = (size_t)(cx - 1) + (size_t)(cy - 1) * m;
-    typename E::Raw rv;
-    if (out) rv = E::ld(a.R, a.rlo, roff + s_node);
+    const int s_node = (cx - 1) + (cy - 1) * m;            // interior index of vertex (cx, cy) (< 2^31)
+    if (out) rv = E::ld(a.R, a.rlo, (size_t)(i - a.rbase) * a.Nx + s_node);
     const bool lo_ok = cy >= 1, hi_ok = cy + 1 <= n - 2;
     const bool oka = okl && lo_ok, okb = okr && lo_ok, okc = okr && hi_ok, okd = okl && hi_ok;
-    const long long ia = (long long)(cx - 1) + (long long)(cy - 1) * m;   // interior index of vertex (cx, cy)
-    const size_t e = (size_t)cxw + (size_t)cy * (n - 1);
+    const int e = cxw + cy * (n - 1);
     typename AR::State st;
     AR::init(st);
 #pragma unroll 2
     for (int t = 0; t < nt; ++t) {
-      const long long q = rt.xo[t] + ia;
-      const T w = AR::template weight<WT>(a, rt.wo[t], e, rt.g[t]);
-      const Z za = oka ? LX::at(a.X, a.xlo, (size_t)q) : LX::zero();
-      const Z zb = okb ? LX::at(a.X, a.xlo, (size_t)(q + 1)) : LX::zero();
-      const Z zc = okc ? LX::at(a.X, a.xlo, (size_t)(q + 1 + m)) : LX::zero();
-      const Z zd = okd ? LX::at(a.X, a.xlo, (size_t)(q + m)) : LX::zero();
+      const XE* p = rt.xp[t] + s_node;                     // vertex (cx, cy) of column j
+      const T w = AR::template weight<WT>(rt.wp[t][e], rt.g[t]);
+      const Z za = oka ? LX::ldp(p, xlo) : LX::zero();
+      const Z zb = okb ? LX::ldp(p + 1, xlo) : LX::zero();
+      const Z zc = okc ? LX::ldp(p + 1 + m, xlo) : LX::zero();
+      const Z zd = okd ? LX::ldp(p + m, xlo) : LX::zero();
       AR::term(st, w, za, zb, zc, zd);
     }
     T Ac, Bc, Cc;
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
         AR::acc_sub(y, Bp);
         AR::acc_sub(y, Cp);
         AR::acc_add(y, ul);
-        Store<TYS>::put(a.Y, a.ylo, yoff + s_node, E::f(rv, AR::get(y)));
+        Store<TYS>::put(a.Y, a.ylo, (size_t)(i - a.ybase) * a.Nx + s_node, E::f(rv, AR::get(y)));
       }
     }
     Ap = Ac, Bp = Bc, Cp = Cc;
