@@ -54,7 +54,12 @@ typedef enum {
  * hi + lo (about 48 significant bits).  It is the internal FP64-class format
  * of the fast solver mode (GB300 runs FP64 arithmetic at 1/68 of its FP32
  * rate); sg_apply accepts it for X and Y. */
-typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2, SG_DF64 = 3 } sg_prec;
+/* SG_BF16Z (preconditioners and sg_solve's pc_prec only): the V-cycle levels and the
+ * stage right-hand sides of the sweeps are stored in BF16 (FP32 arithmetic), the
+ * preconditioned vectors Z = B^{-1} R the call returns are FP32.  Keeping the output
+ * in FP32 avoids the BF16 rounding of the flexible basis z_j, which costs FGMRES
+ * extra iterations, while the multigrid traffic stays at BF16 width. */
+typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2, SG_DF64 = 3, SG_BF16Z = 4 } sg_prec;
 /* Arithmetic of the outer Krylov solver: SG_ARITH_F64 = IEEE FP64 throughout;
  * SG_ARITH_DF64 = the Arnoldi basis, the outer operator A z and the
  * Gram-Schmidt sums in double-float (FP32 pairs with error-free
@@ -95,7 +100,8 @@ typedef struct {
  * recomputed in FP64 at every restart and at the end).  pc_prec: precision of
  * the preconditioner (V-cycle and triangular sweep); the outer Krylov vectors,
  * orthogonalisation, Givens rotations, true residual and coarsest-grid solve
- * are always FP64.  transpose: solve A^T U = F preconditioned by B^T (the
+ * are always FP64 (SG_F64, SG_F32, SG_BF16 or SG_BF16Z; z_j is stored in FP32 for
+ * SG_BF16Z).  transpose: solve A^T U = F preconditioned by B^T (the
  * adjoint solve; B_T^T is the upper block-triangular sweep).  x0_given: U holds
  * an initial guess (else U = 0 is used).  reorth: 0 classical Gram-Schmidt,
  * 1 classical Gram-Schmidt with a second pass when the norm drops by more than

@@ -109,7 +109,7 @@ int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec
   if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, rprec, R, Z, prec, transpose);
   if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, rprec, R, Z, prec);
   if (pc == SG_PC_BLOCKSYM) return precond_blocksym(h, rprec, R, Z, prec);
-  return vec_cast(h, rprec, R, prec, Z, h->Nx * (size_t)h->P);
+  return vec_cast(h, rprec, R, zprec_of(prec), Z, h->Nx * (size_t)h->P);
 }
 
 // Krylov vectors use the padded length Np (multiple of 64) with zero padding, so the
@@ -136,7 +136,8 @@ int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec, int layout = -1) {
     cudaFree(h->kz);
     h->kz = nullptr;
     h->kz_cap = 0;
-    if (cudaMalloc(&h->kz, prec_size(zprec) * N * std::max(nz, 1)) != cudaSuccess)
+    // preconditioned vectors at the padded stride Np, so every z_j starts 128-byte aligned
+    if (cudaMalloc(&h->kz, prec_size(zprec) * Np * std::max(nz, 1)) != cudaSuccess)
       return sg_fail(h, SG_E_ALLOC, "alloc preconditioned basis");
     h->kz_cap = std::max(nz, 1);
     h->kz_prec = zprec;
@@ -163,28 +164,28 @@ struct OpsF64 {
   bool flexible;
   double* V;
   int init() {
-    int rc = ensure_krylov(h, o.restart + 1, flexible ? o.restart : 1, o.pc_prec, 0);
+    int rc = ensure_krylov(h, o.restart + 1, flexible ? o.restart : 1, zprec_of(o.pc_prec), 0);
     V = h->kv;
     return rc;
   }
   double* v(int l) { return V + h->Np * l; }
-  void* z(int j) { return (char*)h->kz + prec_size(o.pc_prec) * N * (flexible ? j : 0); }
+  void* z(int j) { return (char*)h->kz + prec_size(zprec_of(o.pc_prec)) * h->Np * (flexible ? j : 0); }
   int norm2_rhs(double* out) { int rc; *out = host_dot(h, F, F, N, &rc); return rc; }
   int zero_solution() { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
   int residual(bool) { return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F); }
   int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
   int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
-  int apply(int j) { return apply_f64(h, 0, o.pc_prec, z(j), SG_F64, v(j + 1), nullptr); }
+  int apply(int j) { return apply_f64(h, 0, zprec_of(o.pc_prec), z(j), SG_F64, v(j + 1), nullptr); }
   int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
   int axpys(int j, const double* c) { return vec_axpys_norm(h, V, h->Np, j + 1, c, v(j + 1), h->Np, nullptr); }
   int update(int k, const double* y) {
-    if (flexible) return vec_update(h, U, o.pc_prec, h->kz, N, k, y, N);
+    if (flexible) return vec_update(h, U, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N);
     double* t = h->ktmp;
     SG_CUDA(h, cudaMemsetAsync(t, 0, sizeof(double) * N, h->stream));
     int rc;
     if ((rc = vec_update(h, t, SG_F64, V, h->Np, k, y, N))) return rc;
     if ((rc = apply_precond(h, o.precond, SG_F64, t, h->kz, o.pc_prec, o.transpose))) return rc;
-    return vec_axpy_prec(h, 1.0, o.pc_prec, h->kz, U, N);
+    return vec_axpy_prec(h, 1.0, zprec_of(o.pc_prec), h->kz, U, N);
   }
   int finish() { return SG_OK; }
 };
@@ -199,9 +200,9 @@ struct OpsDF {
   float* Fd;   // right-hand side and solution in double-float
   float* Ud;
   int init() {
-    if (o.pc_prec != SG_F32 && o.pc_prec != SG_BF16)
+    if (o.pc_prec != SG_F32 && o.pc_prec != SG_BF16 && o.pc_prec != SG_BF16Z)
       return sg_fail(h, SG_E_ARG, "double-float mode needs an FP32 or BF16 preconditioner");
-    int rc = ensure_krylov(h, o.restart + 1, o.restart, o.pc_prec, 1);
+    int rc = ensure_krylov(h, o.restart + 1, o.restart, zprec_of(o.pc_prec), 1);
     if (rc) return rc;
     const size_t Np = h->Np;
     V = (float*)h->kv;
@@ -213,7 +214,7 @@ struct OpsDF {
     return SG_OK;
   }
   float* v(int l) { return V + 2 * h->Np * l; }
-  void* z(int j) { return (char*)h->kz + prec_size(o.pc_prec) * N * j; }
+  void* z(int j) { return (char*)h->kz + prec_size(zprec_of(o.pc_prec)) * h->Np * j; }
   int norm2_rhs(double* out) {
     int rc;
     if ((rc = df_dots(h, nullptr, 0, 0, Fd, h->Np, true))) return rc;
@@ -240,12 +241,12 @@ struct OpsDF {
   }
   int precond(int j) { return apply_precond(h, o.precond, SG_F32, v(j), z(j), o.pc_prec, o.transpose); }
   int apply(int j) {
-    return launch_apply(h, 0, o.pc_prec, z(j), 0, SG_DF64, v(j + 1), h->Np, SG_DF64, nullptr, 0, 0, h->P, 0, 0,
+    return launch_apply(h, 0, zprec_of(o.pc_prec), z(j), 0, SG_DF64, v(j + 1), h->Np, SG_DF64, nullptr, 0, 0, h->P, 0, 0,
                         SG_DF64);
   }
   int dots(int j, bool ww) { return df_dots(h, V, 2 * h->Np, j + 1, v(j + 1), h->Np, ww); }
   int axpys(int j, const double* c) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, c, v(j + 1), h->Np); }
-  int update(int k, const double* y) { return df_update(h, Ud, h->Np, o.pc_prec, h->kz, N, k, y, N); }
+  int update(int k, const double* y) { return df_update(h, Ud, h->Np, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N); }
   int finish() { return df_to_f64(h, Ud, U, N, h->Np); }
 };
 
@@ -387,7 +388,7 @@ int solve_gmres(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, s
 // direction, alpha = <r,d>/<Ad,d>.
 int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
   const size_t N = h->Nx * (size_t)h->P;
-  const int zp = o.pc_prec;
+  const int pcm = o.pc_prec, zp = zprec_of(pcm);     // preconditioner mode, storage of z
   int rc = ensure_krylov(h, 1, 1, zp);
   if (rc) return rc;
   double *r = h->ktmp, *Ag = h->ktmp + N, *d = h->ktmp + 2 * N, *Ad = h->ktmp + 3 * N;
@@ -403,7 +404,7 @@ int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg
   while (std::sqrt(rr) > o.tol * bnorm) {
     if (!std::isfinite(rr)) return sg_fail(h, SG_E_NONFINITE, "non-finite residual");
     if (its >= o.maxit) { info.iters = its; info.relres_true = std::sqrt(rr) / bnorm; return SG_E_NOCONV; }
-    if ((rc = apply_precond(h, o.precond, SG_F64,r, gv, zp, o.transpose))) return rc;
+    if ((rc = apply_precond(h, o.precond, SG_F64, r, gv, pcm, o.transpose))) return rc;
     if ((rc = apply_f64(h,0, zp, gv, SG_F64, Ag, nullptr))) return rc;
     if (its == 0) {
       if ((rc = vec_cast(h, zp, gv, SG_F64, d, N))) return rc;
@@ -438,7 +439,7 @@ int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg
 // Stationary block Gauss-Seidel (Sec. 4.2, the B-GS rows of Table 3): U += B^{-1}(F - A U).
 int solve_bgs(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
   const size_t N = h->Nx * (size_t)h->P;
-  const int zp = o.pc_prec;
+  const int pcm = o.pc_prec, zp = zprec_of(pcm);     // preconditioner mode, storage of z
   int rc = ensure_krylov(h, 1, 1, zp);
   if (rc) return rc;
   double* r = h->ktmp;
@@ -457,7 +458,7 @@ int solve_bgs(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
     if (its >= o.maxit) { info.iters = its; return SG_E_NOCONV; }
     {
       PhaseScope ps(h, 1);
-      if ((rc = apply_precond(h, o.precond, SG_F64, r, h->kz, zp, o.transpose))) return rc;
+      if ((rc = apply_precond(h, o.precond, SG_F64, r, h->kz, pcm, o.transpose))) return rc;
     }
     if ((rc = vec_axpy_prec(h, 1.0, zp, h->kz, U, N))) return rc;
     ++its;
@@ -468,7 +469,7 @@ int solve_bgs(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
 
 int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_info& info) {
   const size_t N = h->Nx * (size_t)h->P;
-  const int zp = o.pc_prec;
+  const int pcm = o.pc_prec, zp = zprec_of(pcm);     // preconditioner mode, storage of z
   int rc = ensure_krylov(h, 1, 1, zp);
   if (rc) return rc;
   double *r = h->ktmp, *Ad = h->ktmp + N, *d = h->ktmp + 2 * N;
@@ -477,7 +478,7 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
   if (rc) return rc;
   if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
   if ((rc = apply_f64(h,0, SG_F64, U, SG_F64, r, F))) return rc;
-  if ((rc = apply_precond(h, o.precond, SG_F64,r, z, zp, o.transpose))) return rc;
+  if ((rc = apply_precond(h, o.precond, SG_F64, r, z, pcm, o.transpose))) return rc;
   if ((rc = vec_cast(h, zp, z, SG_F64, d, N))) return rc;
   const double* xs0[2] = {r, r};
   const void* ys0[2] = {z, r};
@@ -497,7 +498,7 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
     if ((rc = vec_axpby(h, alpha, d, 1.0, U, N))) return rc;
     if ((rc = vec_axpby(h, -alpha, Ad, 1.0, r, N))) return rc;
     ++its;
-    if ((rc = apply_precond(h, o.precond, SG_F64,r, z, zp, o.transpose))) return rc;
+    if ((rc = apply_precond(h, o.precond, SG_F64, r, z, pcm, o.transpose))) return rc;
     if ((rc = vec_dot_pairs(h, 2, xs0, ys0, yp0, N, t2))) return rc;
     const double beta = t2[0] / rz;
     rz = t2[0], rr = t2[1];
@@ -517,7 +518,7 @@ void destroy_ctx(sg_ctx* h) {
   free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off), free_terms(h->t_diag);
   for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
   for (auto& W : h->work) {
-    cudaFree(W.T), cudaFree(W.S1), cudaFree(W.S2);
+    cudaFree(W.T), cudaFree(W.T32), cudaFree(W.S1), cudaFree(W.S2);
     for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(W.b[l]), cudaFree(W.x[l]);
   }
   cudaFree(h->red_partial), cudaFree(h->red_out), cudaFree(h->red_count), cudaFreeHost(h->red_host);
@@ -665,22 +666,22 @@ int sg_residual(sg_handle h, const double* F, const double* U, double* R) {
 }
 
 int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose) {
-  if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocktri: bad argument") : SG_E_ARG;
+  if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocktri: bad argument") : SG_E_ARG;
   return precond_blocktri(h, SG_F64, R, Z, prec, transpose != 0);
 }
 
 int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec) {
-  if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blockdiag: bad argument") : SG_E_ARG;
+  if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blockdiag: bad argument") : SG_E_ARG;
   return precond_blockdiag(h, SG_F64, R, Z, prec);
 }
 
 int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec) {
-  if (!h || !R || !Z || prec < 0 || prec > 2) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocksym: bad argument") : SG_E_ARG;
+  if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocksym: bad argument") : SG_E_ARG;
   return precond_blocksym(h, SG_F64, R, Z, prec);
 }
 
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
-  if (!h || !B || !X || prec < 0 || prec > 2 || nblocks < 0 || nblocks > h->P)
+  if (!h || !B || !X || prec < 0 || prec > 4 || prec == SG_DF64 || nblocks < 0 || nblocks > h->P)
     return h ? sg_fail(h, SG_E_ARG, "sg_vcycle: bad argument") : SG_E_ARG;
   return vcycle_run(h, prec, nblocks, B, SG_F64, X);
 }
@@ -688,7 +689,8 @@ int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
 int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info_out) {
   if (!h || !F || !U || !opts) return h ? sg_fail(h, SG_E_ARG, "sg_solve: null argument") : SG_E_ARG;
   sg_solve_opts o = *opts;
-  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 3 || o.pc_prec < 0 || o.pc_prec > 2 ||
+  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 3 || o.pc_prec < 0 || o.pc_prec > 4 ||
+      o.pc_prec == SG_DF64 ||
       !(o.tol > 0) || o.maxit < 0)
     return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
   if ((o.method == SG_GMRES || o.method == SG_FGMRES) && (o.restart < 1 || o.restart > 32))
@@ -722,7 +724,7 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
   else rc = solve_bgs(h, dF, dU, o, info);
   if ((rc == SG_OK && !h->true_res_valid) || rc == SG_E_NOCONV) {
     // true residual in FP64
-    int rc2 = ensure_krylov(h, 1, 1, o.pc_prec);
+    int rc2 = ensure_krylov(h, 1, 1, zprec_of(o.pc_prec));
     if (!rc2) rc2 = apply_f64(h,0, SG_F64, dU, SG_F64, h->ktmp, dF);
     double rr = 0, ff = 0;
     if (!rc2) rr = host_dot(h, h->ktmp, h->ktmp, N, &rc2);

@@ -65,28 +65,34 @@ template <typename TS> struct Load;
 template <> struct Load<double> {
   typedef double Z;
   typedef double E;                                  // stored element
-  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return *p; }
+  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __ldg(p); }
+  static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __ldg(p) : 0.0; }
   static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return ((const double*)p)[i]; }
   static __device__ __forceinline__ Z zero() { return 0.0; }
 };
 template <> struct Load<float> {
   typedef float Z;
   typedef float E;
-  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return *p; }
+  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __ldg(p); }
+  static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __ldg(p) : 0.f; }
   static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return ((const float*)p)[i]; }
   static __device__ __forceinline__ Z zero() { return 0.f; }
 };
 template <> struct Load<bf16> {
   typedef float Z;
   typedef bf16 E;
-  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __bfloat162float(__ldg(p)) : 0.f; }
   static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return __bfloat162float(((const bf16*)p)[i]); }
   static __device__ __forceinline__ Z zero() { return 0.f; }
 };
 template <> struct Load<DFS> {
   typedef df2 Z;
   typedef float E;                                   // hi array; the lo array follows at + lo
-  static __device__ __forceinline__ Z ldp(const E* p, size_t lo) { return {p[0], p[lo]}; }
+  static __device__ __forceinline__ Z ldp(const E* p, size_t lo) { return {__ldg(p), __ldg(p + lo)}; }
+  static __device__ __forceinline__ Z ldq(const E* p, size_t lo, bool ok) {
+    return ok ? Z{__ldg(p), __ldg(p + lo)} : Z{0.f, 0.f};
+  }
   static __device__ __forceinline__ Z at(const void* p, size_t lo, size_t i) {
     return {((const float*)p)[i], ((const float*)p)[i + lo]};
   }
@@ -313,6 +319,13 @@ __device__ __forceinline__ df2 shfl_up1(df2 v) {
   return {__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
 }
 
+__device__ __forceinline__ float ldg_ce(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldg_ce(const double* p) { return __ldg(p); }
+__device__ __forceinline__ df2 ldg_ce(const df2* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
 // The row's couplings as shared-memory tables: the coupled column's base pointer, the base
 // pointer of its weight row (mode k, or table slot), and the coupling value.
 template <class AR, typename XE> struct RowTerms {
@@ -365,11 +378,11 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
 #pragma unroll 2
     for (int t = 0; t < nt; ++t) {
       const XE* p = rt.xp[t] + s_node;                     // vertex (cx, cy) of column j
-      const T w = AR::template weight<WT>(rt.wp[t][e], rt.g[t]);
-      const Z za = oka ? LX::ldp(p, xlo) : LX::zero();
-      const Z zb = okb ? LX::ldp(p + 1, xlo) : LX::zero();
-      const Z zc = okc ? LX::ldp(p + 1 + m, xlo) : LX::zero();
-      const Z zd = okd ? LX::ldp(p + m, xlo) : LX::zero();
+      const T w = AR::template weight<WT>(ldg_ce(rt.wp[t] + e), rt.g[t]);
+      const Z za = LX::ldq(p, xlo, oka);
+      const Z zb = LX::ldq(p + 1, xlo, okb);
+      const Z zc = LX::ldq(p + 1 + m, xlo, okc);
+      const Z zd = LX::ldq(p + m, xlo, okd);
       AR::term(st, w, za, zb, zc, zd);
     }
     T Ac, Bc, Cc;

@@ -63,8 +63,8 @@ __device__ void cg_smooth(const TA* b, TA* x, TA* tmp, int m, const TA* st, TA o
   __syncthreads();
 }
 
-template <typename TB, typename TS, typename TA, bool VAR>
-__global__ void __launch_bounds__(512) mg_coarse(const TB* __restrict__ b, TS* __restrict__ x, size_t ldb,
+template <typename TB, typename TS, typename TA, bool VAR, typename TO = TS>
+__global__ void __launch_bounds__(512) mg_coarse(const TB* __restrict__ b, TO* __restrict__ x, size_t ldb,
                                                  size_t ldx, CoarseLevels L, TA omega, int nu1, int nu2) {
   extern __shared__ unsigned char smem_raw[];
   TA* sm = reinterpret_cast<TA*>(smem_raw);
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(512) mg_coarse(const TB* __restrict__ b, TS* _
     __syncthreads();
     for (int s = 0; s < nu2; ++s) cg_smooth<TA, VAR>(bl, xl, tmp, m, st, omega, false);
   }
-  for (int t = threadIdx.x; t < m0 * m0; t += blockDim.x) st_as<TS, TA>(x + (size_t)blk * ldx + t, sx[t]);
+  for (int t = threadIdx.x; t < m0 * m0; t += blockDim.x) st_as<TO, TA>(x + (size_t)blk * ldx + t, sx[t]);
 }
 
 // ---------------------------------------------------------------------------
@@ -173,12 +173,13 @@ int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
   return SG_OK;
 }
 
-template <typename TB, typename TS, typename TA>
-int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TS* x) {
+template <typename TB, typename TS, typename TA, typename TO = TS>
+int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TO* x) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1 && h->nu2 == 1) {
-    const int tx = (F.m + MU_FX - 1) / MU_FX, ty = (F.m + MU_FY - 1) / MU_FY;
-    mg_up_tile<TB, TS, TA><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N,
+    constexpr int FY = mu_fy<TB, TS, TA>();
+    const int tx = (F.m + MU_FX - 1) / MU_FX, ty = (F.m + FY - 1) / FY;
+    mg_up_tile<TB, TS, TA, TO><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N,
                                                                           (TA)(h->omega * 3.0 / 8.0), tx);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
@@ -187,18 +188,18 @@ int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TS* x) {
   const int tx = (F.m + UX - 1) / UX, ty = (F.m + UY - 1) / UY;
   dim3 grid(tx * ty, nb);
   if (h->const_mean)
-    mg_up<TB, TS, TA, false><<<grid, 256, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, nullptr, (TA)h->omega,
+    mg_up<TB, TS, TA, false, TO><<<grid, 256, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, nullptr, (TA)h->omega,
                                                           h->nu1, h->nu2, tx);
   else
-    mg_up<TB, TS, TA, true><<<grid, 256, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, stencil_ptr<TA>(h, l),
+    mg_up<TB, TS, TA, true, TO><<<grid, 256, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, stencil_ptr<TA>(h, l),
                                                          (TA)h->omega, h->nu1, h->nu2, tx);
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
   return SG_OK;
 }
 
-template <typename TB, typename TS, typename TA>
-int run_coarse(sg_ctx* h, int nb, const TB* b, TS* x) {
+template <typename TB, typename TS, typename TA, typename TO = TS>
+int run_coarse(sg_ctx* h, int nb, const TB* b, TO* x) {
   CoarseLevels L{};
   L.nl = h->nlev - h->lc;
   int off = 0;
@@ -212,11 +213,11 @@ int run_coarse(sg_ctx* h, int nb, const TB* b, TS* x) {
   const size_t smem = (size_t)(2 * off + L.m[0] * L.m[0]) * sizeof(TA);
   const size_t ldb = h->lev[h->lc].N;
   if (h->const_mean) {
-    auto kern = mg_coarse<TB, TS, TA, false>;
+    auto kern = mg_coarse<TB, TS, TA, false, TO>;
     if (smem > 48 * 1024) SG_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<nb, 512, smem, h->stream>>>(b, x, ldb, ldb, L, (TA)h->omega, h->nu1, h->nu2);
   } else {
-    auto kern = mg_coarse<TB, TS, TA, true>;
+    auto kern = mg_coarse<TB, TS, TA, true, TO>;
     if (smem > 48 * 1024) SG_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<nb, 512, smem, h->stream>>>(b, x, ldb, ldb, L, (TA)h->omega, h->nu1, h->nu2);
   }
@@ -225,8 +226,8 @@ int run_coarse(sg_ctx* h, int nb, const TB* b, TS* x) {
   return SG_OK;
 }
 
-template <typename TB, typename TS, typename TA>
-int vcycle_t(sg_ctx* h, int nb, const TB* B, TS* X, PrecWork& W) {
+template <typename TB, typename TS, typename TA, typename TO = TS>
+int vcycle_t(sg_ctx* h, int nb, const TB* B, TO* X, PrecWork& W) {
   int rc;
   const int lc = h->lc;
   // descend
@@ -235,11 +236,11 @@ int vcycle_t(sg_ctx* h, int nb, const TB* B, TS* X, PrecWork& W) {
     else rc = run_down<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (TS*)W.b[l + 1]);
     if (rc) return rc;
   }
-  if (lc == 0) rc = run_coarse<TB, TS, TA>(h, nb, B, X);
+  if (lc == 0) rc = run_coarse<TB, TS, TA, TO>(h, nb, B, X);
   else rc = run_coarse<TS, TS, TA>(h, nb, (const TS*)W.b[lc], (TS*)W.x[lc]);
   if (rc) return rc;
   for (int l = lc - 1; l >= 0; --l) {
-    if (l == 0) rc = run_up<TB, TS, TA>(h, 0, nb, B, (const TS*)W.x[1], X);
+    if (l == 0) rc = run_up<TB, TS, TA, TO>(h, 0, nb, B, (const TS*)W.x[1], X);
     else rc = run_up<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (const TS*)W.x[l + 1], (TS*)W.x[l]);
     if (rc) return rc;
   }
@@ -247,8 +248,15 @@ int vcycle_t(sg_ctx* h, int nb, const TB* B, TS* X, PrecWork& W) {
 }
 }  // namespace
 
-int ensure_prec_work(sg_ctx* h, int prec) {
+int ensure_prec_work(sg_ctx* h, int mode) {
+  const int prec = wprec_of(mode);
   PrecWork& W = h->work[prec];
+  if (mode == SG_BF16Z && !W.T32) {
+    int nqmax = 0;
+    for (int q = 0; q <= h->p; ++q) nqmax = std::max(nqmax, h->lvl_off[q + 1] - h->lvl_off[q]);
+    if (cudaMalloc(&W.T32, sizeof(float) * (size_t)nqmax * h->Nx) != cudaSuccess)
+      return sg_fail(h, SG_E_ALLOC, "alloc FP32 stage buffer");
+  }
   if (W.ready) return SG_OK;
   const size_t es = prec_size(prec);
   int nqmax = 0;
@@ -268,7 +276,12 @@ int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X) {
   if (nb > h->P) return sg_fail(h, SG_E_ARG, "vcycle: more blocks than the workspace holds");
   int rc = ensure_prec_work(h, prec);
   if (rc) return rc;
-  PrecWork& W = h->work[prec];
+  PrecWork& W = h->work[wprec_of(prec)];
+  if (prec == SG_BF16Z) {                 // BF16 levels, FP32 output
+    if (bprec == SG_F64) return vcycle_t<double, bf16, float, float>(h, nb, (const double*)B, (float*)X, W);
+    if (bprec == SG_F32) return vcycle_t<float, bf16, float, float>(h, nb, (const float*)B, (float*)X, W);
+    return vcycle_t<bf16, bf16, float, float>(h, nb, (const bf16*)B, (float*)X, W);
+  }
   if (prec == SG_F64) {
     if (bprec != SG_F64) return sg_fail(h, SG_E_ARG, "vcycle: FP64 cycle needs FP64 input");
     return vcycle_t<double, double, double>(h, nb, (const double*)B, (double*)X, W);
@@ -327,7 +340,10 @@ int run_graphed(sg_ctx* h, const void* R, const void* Z, int rprec, int prec, in
 // blocks of one stage are independent and cycled together.
 static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
   int rc;
-  const size_t es = prec_size(prec), rs = prec_size(rprec);
+  // storage of Z, of the work buffers and of the stage right-hand side T (FP32 for SG_BF16Z: the
+  // levels stay BF16, the vectors the Krylov method sees are FP32)
+  const int zp = zprec_of(prec), wp = wprec_of(prec), tp = prec == SG_BF16Z ? SG_F32 : wp;
+  const size_t es = prec_size(zp), rs = prec_size(rprec);
   const int arith = prec == SG_F64 ? SG_F64 : SG_F32;
   for (int s = 0; s <= h->p; ++s) {
     const int q = transpose ? h->p - s : s;
@@ -337,9 +353,10 @@ static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z,
       rc = vcycle_run(h, prec, nq, (const char*)R + rs * (size_t)r0 * h->Nx, rprec, Zq);
     } else {
       // T_q = R_q - sum over the couplings to the previous stage of G_k(i,j) K_k Z_j
-      rc = launch_apply(h, transpose ? 2 : 1, prec, Z, 0, prec, h->work[prec].T, 0, rprec, R, 0, r0, nq, r0, 0, arith);
+      void* T = prec == SG_BF16Z ? h->work[wp].T32 : h->work[wp].T;
+      rc = launch_apply(h, transpose ? 2 : 1, zp, Z, 0, tp, T, 0, rprec, R, 0, r0, nq, r0, 0, arith);
       if (rc) return rc;
-      rc = vcycle_run(h, prec, nq, h->work[prec].T, prec, Zq);
+      rc = vcycle_run(h, prec, nq, T, tp, Zq);
     }
     if (rc) return rc;
   }
@@ -356,16 +373,22 @@ int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int
 // diagonal blocks K_0 (one stencil pass) and an upper sweep.
 int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
   if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blocksym: FP64 sweep needs FP64 input");
-  PrecWork& W = h->work[prec];
+  const int zp = zprec_of(prec);
+  int rc = ensure_prec_work(h, prec);
+  if (rc) return rc;
+  PrecWork& W = h->work[wprec_of(prec)];
   const size_t N = h->Nx * (size_t)h->P;
   const int sprec = prec == SG_F64 ? SG_F64 : SG_F32;
-  if (!W.S1) {
-    if (cudaMalloc(&W.S1, prec_size(prec) * N) != cudaSuccess || cudaMalloc(&W.S2, prec_size(sprec) * N) != cudaSuccess)
+  if (!W.S1 || W.s1_prec != zp) {
+    cudaFree(W.S1);
+    cudaFree(W.S2);
+    W.S1 = W.S2 = nullptr;
+    if (cudaMalloc(&W.S1, prec_size(zp) * N) != cudaSuccess || cudaMalloc(&W.S2, prec_size(sprec) * N) != cudaSuccess)
       return sg_fail(h, SG_E_ALLOC, "alloc symmetric sweep buffers");
+    W.s1_prec = zp;
   }
-  int rc;
   if ((rc = precond_blocktri(h, rprec, R, W.S1, prec, 0))) return rc;
-  if ((rc = launch_apply(h, 4, prec, W.S1, 0, sprec, W.S2, 0, SG_F64, nullptr, 0, 0, h->P, 0, 0, sprec))) return rc;
+  if ((rc = launch_apply(h, 4, zp, W.S1, 0, sprec, W.S2, 0, SG_F64, nullptr, 0, 0, h->P, 0, 0, sprec))) return rc;
   return precond_blocktri(h, sprec, W.S2, Z, prec, 1);
 }
 

@@ -166,20 +166,47 @@ __global__ void __launch_bounds__(NT) k_axpys_df(const float* __restrict__ V, si
   reduce_out<1>(acc, partial, out, counter, 1);
 }
 
-template <typename TZ, int NV>
+// U += sum_l y_l Z_l for a double-float U (hi at U, lo at U + lo) and nz FP32/BF16 vectors at
+// stride ldz; four elements per thread with 16-byte (8-byte for BF16) loads.  ldz and lo are
+// multiples of 4 and the arrays 16-byte aligned; elements at and beyond N are left unchanged.
+template <typename TZ> struct Z4;
+template <> struct Z4<float> {
+  static __device__ __forceinline__ float4 ld(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+};
+template <> struct Z4<bf16> {
+  static __device__ __forceinline__ float4 ld(const bf16* p) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u), __uint_as_float(r.y << 16),
+                       __uint_as_float(r.y & 0xffff0000u));
+  }
+};
+
+template <typename TZ>
 __global__ void k_update_df(float* __restrict__ U, const TZ* __restrict__ Z, size_t ldz, int nz,
                             const double* __restrict__ y, size_t N, size_t lo) {
-  df2 c[NV];
-#pragma unroll
-  for (int l = 0; l < NV; ++l) c[l] = (l < nz) ? df_from_double(y[l]) : df2{0.f, 0.f};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    dacc u = dacc_from(ldf(U, lo, i));
-#pragma unroll
-    for (int l = 0; l < NV; ++l)
-      if (l < nz) dacc_fma(u, c[l], ld_as<float>(Z + (size_t)l * ldz + i));
-    const df2 r = dacc_get(u);
-    U[i] = r.hi;
-    U[i + lo] = r.lo;
+  __shared__ df2 cs[SG_MAX_RESTART];
+  for (int l = threadIdx.x; l < nz; l += blockDim.x) cs[l] = df_from_double(y[l]);
+  __syncthreads();
+  const size_t n4 = (N + 3) / 4;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = 4 * q;
+    const float4 uh = reinterpret_cast<const float4*>(U)[q], ul = reinterpret_cast<const float4*>(U + lo)[q];
+    dacc u0 = {uh.x, ul.x}, u1 = {uh.y, ul.y}, u2 = {uh.z, ul.z}, u3 = {uh.w, ul.w};
+#pragma unroll 4
+    for (int l = 0; l < nz; ++l) {
+      const float4 z = Z4<TZ>::ld(Z + (size_t)l * ldz + i);
+      const df2 c = cs[l];
+      dacc_fma(u0, c, z.x);
+      dacc_fma(u1, c, z.y);
+      dacc_fma(u2, c, z.z);
+      dacc_fma(u3, c, z.w);
+    }
+    df2 r0 = dacc_get(u0), r1 = dacc_get(u1), r2 = dacc_get(u2), r3 = dacc_get(u3);
+    if (i + 1 >= N) r1 = {uh.y, ul.y};
+    if (i + 2 >= N) r2 = {uh.z, ul.z};
+    if (i + 3 >= N) r3 = {uh.w, ul.w};
+    reinterpret_cast<float4*>(U)[q] = make_float4(r0.hi, r1.hi, r2.hi, r3.hi);
+    reinterpret_cast<float4*>(U + lo)[q] = make_float4(r0.lo, r1.lo, r2.lo, r3.lo);
   }
 }
 
@@ -416,22 +443,19 @@ int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t l
               size_t N) {
   int rc = ensure_reduction(h);
   if (rc) return rc;
-  const size_t es = prec_size(zprec);
-  for (int c0 = 0; c0 < nz; c0 += 16) {
-    const int cn = std::min(16, nz - c0);
-    double* ydev = h->red_out + 2 * MAXOUT;
-    std::copy(y_host + c0, y_host + c0 + cn, h->red_host + 2 * MAXOUT);
-    SG_CUDA(h, cudaMemcpyAsync(ydev, h->red_host + 2 * MAXOUT, sizeof(double) * cn, cudaMemcpyHostToDevice, h->stream));
-    const void* Zc = (const char*)Z + es * (size_t)c0 * ldz;
-    if (zprec == SG_F32)
-      k_update_df<float, 16><<<grid_for(N), 256, 0, h->stream>>>(U, (const float*)Zc, ldz, cn, ydev, N, lo);
-    else if (zprec == SG_BF16)
-      k_update_df<bf16, 16><<<grid_for(N), 256, 0, h->stream>>>(U, (const bf16*)Zc, ldz, cn, ydev, N, lo);
-    else return sg_fail(h, SG_E_ARG, "df update: Z must be FP32 or BF16");
-    SG_CUDA(h, cudaGetLastError());
-    count_launch(h);
-    SG_CUDA(h, cudaStreamSynchronize(h->stream));
-  }
+  if (nz <= 0) return SG_OK;
+  if (nz > MAXOUT || ldz % 4 || lo % 4) return sg_fail(h, SG_E_ARG, "df update: bad layout");
+  double* ydev = h->red_out + 2 * MAXOUT;
+  std::copy(y_host, y_host + nz, h->red_host + 2 * MAXOUT);
+  SG_CUDA(h, cudaMemcpyAsync(ydev, h->red_host + 2 * MAXOUT, sizeof(double) * nz, cudaMemcpyHostToDevice, h->stream));
+  const int g = grid_for((N + 3) / 4);
+  if (zprec == SG_F32) k_update_df<float><<<g, 256, 0, h->stream>>>(U, (const float*)Z, ldz, nz, ydev, N, lo);
+  else if (zprec == SG_BF16) k_update_df<bf16><<<g, 256, 0, h->stream>>>(U, (const bf16*)Z, ldz, nz, ydev, N, lo);
+  else return sg_fail(h, SG_E_ARG, "df update: Z must be FP32 or BF16");
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  // the host staging slot is reused by the next call: wait for this copy
+  SG_CUDA(h, cudaStreamSynchronize(h->stream));
   return SG_OK;
 }
 

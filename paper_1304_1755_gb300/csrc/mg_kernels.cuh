@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(256) mg_down(const TB* __restrict__ b, TS* __r
 }
 
 // level l+1 -> l: recompute x_pre = S^{nu1}(b) from zero, x = x_pre + P x_c, nu2 post-smoothing steps.
-template <typename TB, typename TS, typename TA, bool VAR>
+template <typename TB, typename TS, typename TA, bool VAR, typename TO = TS>
 __global__ void __launch_bounds__(256) mg_up(const TB* __restrict__ b, const TS* __restrict__ xcoarse,
-                                             TS* __restrict__ x, int m, int mc, size_t ldb, size_t ldc, size_t ldx,
+                                             TO* __restrict__ x, int m, int mc, size_t ldb, size_t ldc, size_t ldx,
                                              const TA* __restrict__ st, TA omega, int nu1, int nu2, int tiles_x) {
   __shared__ TA sb[UWX * UWY], sx0[UWX * UWY], sx1[UWX * UWY], sxc[UCX * UCY];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -194,11 +194,11 @@ __global__ void __launch_bounds__(256) mg_up(const TB* __restrict__ b, const TS*
     __syncthreads();
     TA* tmp = xc; xc = xn; xn = tmp;
   }
-  TS* xb = x + (size_t)blk * ldx;
+  TO* xb = x + (size_t)blk * ldx;
   for (int oj = ty; oj < UY; oj += 8)
     for (int oi = tx; oi < UX; oi += 32) {
       const int i = X0 + oi, j = Y0 + oj;
-      if (i < m && j < m) st_as<TS, TA>(xb + (size_t)i + (size_t)j * m, xc[(j - fj0) * WX + (i - fi0)]);
+      if (i < m && j < m) st_as<TO, TA>(xb + (size_t)i + (size_t)j * m, xc[(j - fj0) * WX + (i - fi0)]);
     }
 }
 #undef SG_WLOOP

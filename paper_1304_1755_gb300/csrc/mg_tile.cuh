@@ -21,7 +21,12 @@
 namespace {
 constexpr int MT_THREADS = 256;
 constexpr int MD_TX = 64, MD_TY = 16;     // down: coarse tile (columns x rows)
-constexpr int MU_FX = 128, MU_FY = 32;    // up: fine tile (columns x rows)
+constexpr int MU_FX = 128;                // up: fine tile columns; rows: mu_fy<TB, TS>()
+// rows of the up tile: 32 for 2-byte storage, 16 for wider storage, 8 for FP64 arithmetic (the
+// window, g and the b/e part are staged in shared memory, which stays below 48 KB)
+template <typename TB, typename TS, typename TA> constexpr int mu_fy() {
+  return sizeof(TA) == 8 ? 8 : (sizeof(TB) + sizeof(TS) <= 4 ? 32 : 16);
+}
 
 template <typename T> __device__ __forceinline__ T zero_of() { return T(0); }
 template <> __device__ __forceinline__ bf16 zero_of<bf16>() { return __float2bfloat16_rn(0.f); }
@@ -149,70 +154,80 @@ __global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// up: tile of MU_FX x MU_FY fine nodes starting at (X0, Y0) (both even).  b window: fine
-// rows Y0-1 .. Y0+MU_FY, columns X0-1 .. X0+MU_FX; x_c window: coarse rows Y0/2-1 ..
-// Y0/2+MU_FY/2, columns X0/2-1 .. X0/2+MU_FX/2.  Fine node i lies between coarse nodes
-// (i-1)>>1 and i>>1 (the same node for odd i).  Warp w: fine columns X0 + 64 (w & 1) +
-// 2 lane + {0, 1}, fine rows Y0 + 8 (w >> 1) .. +7.
-template <typename TB, typename TS, typename TA>
+// up: tile of MU_FX x MU_FY fine nodes starting at (X0, Y0) (both even), in two passes.
+// Pass 1 takes the window of fine nodes Y0-1 .. Y0+MU_FY (rows) x X0-1 .. X0+MU_FX (columns) in
+// 2 x 2 blocks: block (R, C) holds fine nodes (2R+1, 2C+1) on coarse node (R, C), (2R+1, 2C+2),
+// (2R+2, 2C+1) and (2R+2, 2C+2) between it and (R, C+1), (R+1, C), (R+1, C+1), so the bilinear
+// prolongation e = P x_c needs the same four coarse values for all four fine nodes.  It stores
+// g = (c^2/3) b + (c/3) e (zero outside the grid) for the whole window and
+// (2c - 3c^2) b + (1 - 3c) e for the tile's own nodes, in shared memory (arithmetic type).  Pass 2 adds
+// the 3 x 3 box sum of g: a thread owns two fine columns and walks eight rows with the
+// horizontal three-sums in registers.
+template <typename TB, typename TS, typename TA, typename TO = TS>
 __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ b, const TS* __restrict__ xc,
-                                                         TS* __restrict__ x, int m, int mc, size_t ldb, size_t ldc,
+                                                         TO* __restrict__ x, int m, int mc, size_t ldb, size_t ldc,
                                                          size_t ldx, TA c, int tiles_x) {
+  constexpr int MU_FY = mu_fy<TB, TS, TA>(), RW = MU_FY / 4;   // tile rows, rows per warp in pass 2
   constexpr int NRB = MU_FY + 2, NCB = MU_FX + 2, SWB = win_pitch<TB, NCB>();
-  constexpr int NRC = MU_FY / 2 + 2, NCC = MU_FX / 2 + 2, SWC = win_pitch<TS, NCC>();
+  constexpr int NRC = MU_FY / 2 + 3, NCC = MU_FX / 2 + 3, SWC = win_pitch<TS, NCC>();
+  constexpr int BR = NRB / 2, BC = NCB / 2;      // 2 x 2 blocks of the window
   __shared__ __align__(16) TB sb[NRB * SWB];
   __shared__ __align__(16) TS sc[NRC * SWC];
   __shared__ int phb[NRB], phc[NRC];
+  __shared__ TA sg[NRB][NCB];                    // g over the window
+  __shared__ TA se[MU_FY][MU_FX];                // the b, e part of the tile's own nodes
   const int X0 = (blockIdx.x % tiles_x) * MU_FX, Y0 = (blockIdx.x / tiles_x) * MU_FY;
   load_window<TB, NRB, NCB>(b + (size_t)blockIdx.y * ldb, m, Y0 - 1, X0 - 1, sb, phb);
   load_window<TS, NRC, NCC>(xc + (size_t)blockIdx.y * ldc, mc, Y0 / 2 - 1, X0 / 2 - 1, sc, phc);
   cp_async_wait_all();
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k0 = 64 * (warp & 1) + 2 * lane;      // fine column offset of i0 within the tile
-  const int i0 = X0 + k0, i1 = i0 + 1;
-  const int jw = 8 * (warp >> 1);                 // first fine row offset of this warp
   const TA cgb = c * c / TA(3), cge = c / TA(3), cbb = TA(2) * c - TA(3) * c * c, cee = TA(1) - TA(3) * c;
-  // coarse window column of coarse node C = X0/2 + k0/2 (the node under i1) is k0/2 + 1
-  const int cc = k0 / 2 + 1;
-  const bool okm = i0 - 1 >= 0 && i0 - 1 < m, ok0 = i0 < m, ok1 = i1 < m, okp = i1 + 1 < m;
-  TA H0[10], H1[10], be0[8], be1[8];
+  // pass 1: block (br, bc) of the window = coarse node (Y0/2 - 1 + br, X0/2 - 1 + bc) = window
+  // coarse row br, column bc; its fine nodes are window rows 2br, 2br+1 and columns 2bc, 2bc+1
+  for (int t = threadIdx.x; t < BR * BC; t += MT_THREADS) {
+    const int br = t / BC, bc = t - br * BC;
+    const TS* c0 = sc + br * SWC + phc[br] + bc;
+    const TS* c1 = sc + (br + 1) * SWC + phc[br + 1] + bc;
+    const TA x00 = sld<TA>(c0), x01 = sld<TA>(c0 + 1), x10 = sld<TA>(c1), x11 = sld<TA>(c1 + 1);
+    const TA e[2][2] = {{x00, TA(0.5) * (x00 + x01)},
+                        {TA(0.5) * (x00 + x10), TA(0.25) * ((x00 + x01) + (x10 + x11))}};
 #pragma unroll
-  for (int k = 0; k < 10; ++k) {
-    const int jr = jw + k - 1;                    // fine row offset from Y0 (-1 .. 32)
-    const int j = Y0 + jr;
-    const bool jok = j >= 0 && j < m;
-    // coarse rows under fine row j: lo = (j-1)>>1, hi = j>>1 (window rows + 1 - Y0/2)
-    const int rlo = ((jr - 1) >> 1) + 1, rhi = (jr >> 1) + 1;
-    const TA wa = (j & 1) ? TA(1) : TA(0.5), wb = (j & 1) ? TA(0) : TA(0.5);
-    const TS* clo = sc + rlo * SWC + phc[rlo] + cc;
-    const TS* chi = sc + rhi * SWC + phc[rhi] + cc;
-    const TA em1 = wa * sld<TA>(clo - 1) + wb * sld<TA>(chi - 1);   // coarse C-1 at row j
-    const TA e_c = wa * sld<TA>(clo) + wb * sld<TA>(chi);           // coarse C
-    const TA ep1 = wa * sld<TA>(clo + 1) + wb * sld<TA>(chi + 1);   // coarse C+1
-    // prolongation to the four fine columns i0-1 (odd, on C-1), i0 (even), i1 (odd, on C), i1+1
-    const TA e_m = em1, e_0 = TA(0.5) * (em1 + e_c), e_1 = e_c, e_p = TA(0.5) * (e_c + ep1);
-    const TB* brow = sb + (jr + 1) * SWB + phb[jr + 1] + k0;         // window column of i0 - 1
-    const TA b_m = sld<TA>(brow), b_0 = sld<TA>(brow + 1), b_1 = sld<TA>(brow + 2), b_p = sld<TA>(brow + 3);
-    const TA g_m = jok && okm ? cgb * b_m + cge * e_m : TA(0);
-    const TA g_0 = jok && ok0 ? cgb * b_0 + cge * e_0 : TA(0);
-    const TA g_1 = jok && ok1 ? cgb * b_1 + cge * e_1 : TA(0);
-    const TA g_p = jok && okp ? cgb * b_p + cge * e_p : TA(0);
-    H0[k] = (g_m + g_0) + g_1;
-    H1[k] = (g_0 + g_1) + g_p;
-    if (k >= 1 && k <= 8) {
-      be0[k - 1] = cbb * b_0 + cee * e_0;
-      be1[k - 1] = cbb * b_1 + cee * e_1;
+    for (int dy = 0; dy < 2; ++dy) {
+      const int rr = 2 * br + dy;                 // window row; fine row Y0 - 1 + rr
+      const int j = Y0 - 1 + rr;
+      const TB* brow = sb + rr * SWB + phb[rr] + 2 * bc;
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int cw = 2 * bc + dx, i = X0 - 1 + cw;
+        const TA bv = sld<TA>(brow + dx);
+        const bool in = j >= 0 && j < m && i >= 0 && i < m;
+        sg[rr][cw] = in ? cgb * bv + cge * e[dy][dx] : TA(0);
+        if (rr >= 1 && rr <= MU_FY && cw >= 1 && cw <= MU_FX) se[rr - 1][cw - 1] = cbb * bv + cee * e[dy][dx];
+      }
     }
   }
-  TS* xb = x + (size_t)blockIdx.y * ldx;
+  __syncthreads();
+  // pass 2: thread columns k0, k0 + 1 of the tile, rows jw .. jw + RW - 1
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k0 = 64 * (warp & 1) + 2 * lane;
+  const int jw = RW * (warp >> 1);
+  const int i0 = X0 + k0, i1 = i0 + 1;
+  TA H0[RW + 2], H1[RW + 2];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int k = 0; k < RW + 2; ++k) {              // window rows jw .. jw + RW + 1 = fine rows Y0 + jw - 1 ..
+    const TA* gr = &sg[jw + k][k0];               // window columns k0 .. k0 + 3 = fine i0 - 1 .. i1 + 1
+    const TA gm = gr[0], g0 = gr[1], g1 = gr[2], gp = gr[3];
+    H0[k] = (gm + g0) + g1;
+    H1[k] = (g0 + g1) + gp;
+  }
+  TO* xb = x + (size_t)blockIdx.y * ldx;
+#pragma unroll
+  for (int q = 0; q < RW; ++q) {
     const int j = Y0 + jw + q;
     if (j < m) {
-      TS* op = xb + (size_t)j * m;
-      if (ok0) st_as<TS, TA>(op + i0, be0[q] + ((H0[q] + H0[q + 1]) + H0[q + 2]));
-      if (ok1) st_as<TS, TA>(op + i1, be1[q] + ((H1[q] + H1[q + 1]) + H1[q + 2]));
+      TO* op = xb + (size_t)j * m;
+      if (i0 < m) st_as<TO, TA>(op + i0, se[jw + q][k0] + ((H0[q] + H0[q + 1]) + H0[q + 2]));
+      if (i1 < m) st_as<TO, TA>(op + i1, se[jw + q][k0 + 1] + ((H1[q] + H1[q + 1]) + H1[q + 2]));
     }
   }
 }

@@ -51,10 +51,12 @@ struct MGLevel {
 struct PrecWork {
   bool ready = false;
   void* T = nullptr;                    // stage right-hand side, n_q_max * N_x
+  void* T32 = nullptr;                  // FP32 stage right-hand side (SG_BF16Z sweeps), n_q_max * N_x
   void* b[SG_MAX_LEVELS] = {};          // level >= 1 right-hand sides, P * N_l
   void* x[SG_MAX_LEVELS] = {};          // level >= 1 solutions, P * N_l
   void* S1 = nullptr;                   // symmetric sweep: lower-sweep result (P * N_x)
   void* S2 = nullptr;                   //                  K_0 times it, FP32 (FP64 for an FP64 sweep)
+  int s1_prec = -1;                     // storage precision of S1
 };
 
 // Per-phase event tracing (sg_timing_*).  Phase 0 outer operator, 1 preconditioner,
@@ -159,6 +161,10 @@ int sg_fail(sg_ctx* h, int code, const std::string& msg);
   } while (0)
 
 size_t prec_size(int prec);
+// Preconditioner modes: the storage precision of the returned vectors Z and of the work
+// buffers (levels, stage right-hand sides).  Only SG_BF16Z differs: BF16 work, FP32 Z.
+inline int zprec_of(int mode) { return mode == SG_BF16Z ? SG_F32 : mode; }
+inline int wprec_of(int mode) { return mode == SG_BF16Z ? SG_BF16 : mode; }
 
 // setup.cpp
 int kl_coef_host(int n, int M, double sigma, double corr_len, const double* abar, double* coef, double* lam);

@@ -12,7 +12,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsg.so")
 
-F64, F32, BF16, DF64 = 0, 1, 2, 3
+F64, F32, BF16, DF64, BF16Z = 0, 1, 2, 3, 4   # BF16Z: BF16 preconditioner storage, FP32 output
 ARITH_F64, ARITH_DF64 = 0, 1
 LEGENDRE, HERMITE = 0, 1
 GMRES, FGMRES, GPCG, PCG, BGS = 0, 1, 2, 3, 4

@@ -164,7 +164,7 @@ PC_SHAPES = [(9, 2, 3, basis.LEGENDRE, "one"), (33, 2, 2, basis.LEGENDRE, "one")
 
 @pytest.mark.parametrize("shape", PC_SHAPES, ids=lambda s: f"n{s[0]}M{s[1]}p{s[2]}{s[4]}")
 @pytest.mark.parametrize("kind", ["tri", "tri_T", "diag", "sym"])
-@pytest.mark.parametrize("prec", [0, 1, 2], ids=["f64", "f32", "bf16"])
+@pytest.mark.parametrize("prec", [0, 1, 2, 4], ids=["f64", "f32", "bf16", "bf16z"])
 def test_preconditioners(shape, kind, prec):
     import torch
     n, M, p, fam, mean = shape
@@ -177,7 +177,7 @@ def test_preconditioners(shape, kind, prec):
         ref = precond.block_sym_inv(pr.sys, solver, R)
     else:
         ref = precond.block_tri_inv(pr.sys, solver, R, transpose=(kind == "tri_T"))
-    dt = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[prec]
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16, 4: torch.float32}[prec]
     Z = torch.empty(pr.N, dtype=dt, device="cuda")
     if kind == "diag":
         pr.h.precond_blockdiag(dev(R), Z, prec)

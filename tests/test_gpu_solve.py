@@ -36,6 +36,8 @@ CASES = [  # method, precond, pc_prec, restart
     (sg.PCG, sg.PC_BLOCKDIAG, sg.F64, 0),
     (sg.FGMRES, sg.PC_BLOCKTRI, sg.F32, 30),
     (sg.FGMRES, sg.PC_BLOCKTRI, sg.BF16, 30),
+    (sg.FGMRES, sg.PC_BLOCKTRI, sg.BF16Z, 30),
+    (sg.GPCG, sg.PC_BLOCKTRI, sg.BF16Z, 0),
     (sg.FGMRES, sg.PC_NONE, sg.F64, 30),
     (sg.PCG, sg.PC_BLOCKSYM, sg.F64, 0),
     (sg.FGMRES, sg.PC_BLOCKSYM, sg.F32, 30),
@@ -97,7 +99,9 @@ def test_solves_other_shapes(n, M, p, fam, mean):
 @pytest.mark.parametrize("n,M,p,fam,mean,pcp", [(33, 2, 2, basis.LEGENDRE, "one", sg.F32),
                                                  (33, 2, 2, basis.LEGENDRE, "one", sg.BF16),
                                                  (65, 3, 3, basis.HERMITE, "lognormal", sg.BF16),
-                                                 (129, 2, 2, basis.LEGENDRE, "one", sg.F32)])
+                                                 (129, 2, 2, basis.LEGENDRE, "one", sg.F32),
+                                                 (65, 3, 3, basis.HERMITE, "lognormal", sg.BF16Z),
+                                                 (129, 2, 2, basis.LEGENDRE, "one", sg.BF16Z)])
 def test_double_float_fgmres_matches_direct(n, M, p, fam, mean, pcp):
     """Double-float Arnoldi basis and operator (SG_ARITH_DF64): same bar as FP64 runs."""
     import torch
