@@ -55,6 +55,7 @@ WORKLOADS = {
                name="sg_c5_batch64_uneven_65to513sq_M2to6_p2to4_legendre_fgmres30_fp32pc"),
 }
 PREC_NAME = {0: "f64", 1: "f32", 2: "bf16", 4: "bf16 storage, f32 output"}
+ZNAME = {0: "f64", 1: "f32", 2: "bf16", 4: "f32"}              # storage of the preconditioned vectors z
 METRIC = "time to rel. residual 1e-8 (block-tri GMRES+MG) and SG-apply HBM GB/s"
 C5_METRIC = "aggregate unknowns solved per second (64 uneven SG systems, block-tri FGMRES+MG to 1e-8)"
 
@@ -245,6 +246,23 @@ def run_ours(args, wl, rank, world):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
+    # the other preconditioner storage variants of the same solve (context for the precision choice)
+    variants = {}
+    if args.workload == "c3" and not args.no_fp64_compare:
+        for name, pcp in (("bf16 levels, bf16 z", sg.BF16), ("f32 levels, f32 z", sg.F32)):
+            o2 = dict(opts, pc_prec=pcp)
+            U2 = torch.zeros_like(U)
+            h.solve(F, U2, **o2)
+            torch.cuda.synchronize()
+            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+            for _ in range(args.steps):
+                i2 = h.solve(F, U2, **o2)
+            e3.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = {"ms_per_step": round(e2.elapsed_time(e3) / args.steps, 3), "iterations": i2.iters,
+                              "relres_true": i2.relres_true}
+            del U2
     # the same solve in plain FP64 (FP64 preconditioner, FP64 Krylov arithmetic) on the same GPU
     vs64 = None
     if not args.no_fp64_compare and (wl["pc_prec"] != sg.F64 or arith != sg.ARITH_F64):
@@ -296,6 +314,7 @@ def run_ours(args, wl, rank, world):
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "clocks": clocks,
         "vs_plain_fp64": vs64,
+        "preconditioner_variants": variants or None,
     }
     # C2's comparison: sigma in {0.1, 0.3, 0.5}, block-triangular vs block-diagonal, FP64 vs FP32
     # preconditioner inside FP64 flexible GMRES (one timed solve each, same grid and chaos space)
@@ -311,8 +330,8 @@ def run_ours(args, wl, rank, world):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if df else 1.25
     out["roofline"] = {
-        "kernel": "k_apply<ArDF, bf16, DFS> (outer SG operator, double-float)" if df else
-                  "k_apply<ArF64> (outer SG operator, FP64)",
+        "kernel": (f"k_apply<ArDF, {ZNAME[wl['pc_prec']]} z, double-float w> (outer SG operator)" if df else
+                   "k_apply<ArF64> (outer SG operator, FP64)"),
         "dominant_phase": names[dom],
         "bound": "alu",
         "achieved": round(achieved, 2),

@@ -343,7 +343,9 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   typedef Epi<AR, TRS> E;
   typedef typename LX::E XE;
   __shared__ RowTerms<AR, XE> rt;
-  const int i = a.row0 + blockIdx.y;                       // output row of this CTA
+  // rows vary fastest across the grid, so every row's CTAs over one grid tile run close together
+  // and the coupled columns' tile is read from HBM once and then from L2
+  const int i = a.row0 + blockIdx.x;                       // output row of this CTA
   const int t0 = a.row_ptr[i];
   const int nt = a.row_ptr[i + 1] - t0;                    // <= MAXT (M <= 16 at set-up)
   for (int t = threadIdx.x; t < nt; t += NT) {
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
     rt.g[t] = AR::gval(a, t0 + t);
   }
   __syncthreads();
-  const int gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const int gw = blockIdx.y * WARPS + (threadIdx.x >> 5);
   if (gw >= a.nwx * a.nstrips) return;                     // whole warps only
   const int lane = threadIdx.x & 31;
   const int n = a.n, m = a.m;
@@ -413,14 +415,18 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
 
 template <class AR, typename TXS, typename TYS, typename TRS>
 int launch_t(sg_ctx* h, ApplyArgs& a) {
-  if (a.nrows > 65535) return sg_fail(h, SG_E_ARG, "apply: more than 65535 rows in one launch");
   a.nwx = (h->m + 30) / 31;
-  a.nstrips = (h->m + a.strip - 1) / a.strip;
-  const unsigned gx = (unsigned)(((long)a.nwx * a.nstrips + WARPS - 1) / WARPS);
+  long gy;
+  for (;;) {                                 // taller strips when the grid would exceed 65535 CTAs per row
+    a.nstrips = (h->m + a.strip - 1) / a.strip;
+    gy = ((long)a.nwx * a.nstrips + WARPS - 1) / WARPS;
+    if (gy <= 65535) break;
+    a.strip *= 2;
+  }
   if (AR::kUsesTable && a.wdf)
-    k_apply<AR, true, TXS, TYS, TRS><<<dim3(gx, (unsigned)a.nrows), NT, 0, h->stream>>>(a);
+    k_apply<AR, true, TXS, TYS, TRS><<<dim3((unsigned)a.nrows, (unsigned)gy), NT, 0, h->stream>>>(a);
   else
-    k_apply<AR, false, TXS, TYS, TRS><<<dim3(gx, (unsigned)a.nrows), NT, 0, h->stream>>>(a);
+    k_apply<AR, false, TXS, TYS, TRS><<<dim3((unsigned)a.nrows, (unsigned)gy), NT, 0, h->stream>>>(a);
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
   return SG_OK;
