@@ -61,40 +61,31 @@ struct ApplyArgs {
 // ---- storage access --------------------------------------------------------
 struct DFS {};   // tag: double-float storage, hi array at p, lo array at p + lo
 
+// ldq: the element at p as the policy's input type when ok, else zero (nothing is read when ok is false)
 template <typename TS> struct Load;
 template <> struct Load<double> {
   typedef double Z;
   typedef double E;                                  // stored element
-  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __ldg(p); }
   static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __ldg(p) : 0.0; }
-  static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return ((const double*)p)[i]; }
   static __device__ __forceinline__ Z zero() { return 0.0; }
 };
 template <> struct Load<float> {
   typedef float Z;
   typedef float E;
-  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __ldg(p); }
   static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __ldg(p) : 0.f; }
-  static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return ((const float*)p)[i]; }
   static __device__ __forceinline__ Z zero() { return 0.f; }
 };
 template <> struct Load<bf16> {
   typedef float Z;
   typedef bf16 E;
-  static __device__ __forceinline__ Z ldp(const E* p, size_t) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __bfloat162float(__ldg(p)) : 0.f; }
-  static __device__ __forceinline__ Z at(const void* p, size_t, size_t i) { return __bfloat162float(((const bf16*)p)[i]); }
   static __device__ __forceinline__ Z zero() { return 0.f; }
 };
 template <> struct Load<DFS> {
   typedef df2 Z;
   typedef float E;                                   // hi array; the lo array follows at + lo
-  static __device__ __forceinline__ Z ldp(const E* p, size_t lo) { return {__ldg(p), __ldg(p + lo)}; }
   static __device__ __forceinline__ Z ldq(const E* p, size_t lo, bool ok) {
     return ok ? Z{__ldg(p), __ldg(p + lo)} : Z{0.f, 0.f};
-  }
-  static __device__ __forceinline__ Z at(const void* p, size_t lo, size_t i) {
-    return {((const float*)p)[i], ((const float*)p)[i + lo]};
   }
   static __device__ __forceinline__ Z zero() { return {0.f, 0.f}; }
 };
@@ -123,6 +114,7 @@ template <> struct Load<DFS> {
 
 struct ArF32 {
   static constexpr bool kUsesTable = false;
+  static constexpr int kUnroll = 4;        // couplings in flight per step (latency-bound stage updates)
   typedef float T;
   typedef float Acc;
   typedef float G;
@@ -147,6 +139,7 @@ struct ArF32 {
 
 struct ArF64 {
   static constexpr bool kUsesTable = false;
+  static constexpr int kUnroll = 2;
   typedef double T;
   typedef double Acc;
   typedef double G;
@@ -174,6 +167,7 @@ struct ArDF {
   typedef dacc Acc;
   // with the weight table, k is the term's weight slot (precomputed c_k(e) gamma products)
   static constexpr bool kUsesTable = true;
+  static constexpr int kUnroll = 2;
   typedef df2 G;
   typedef df2 CE;
   static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.gdf[t]; }
@@ -377,7 +371,7 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
     const int e = cxw + cy * (n - 1);
     typename AR::State st;
     AR::init(st);
-#pragma unroll 2
+#pragma unroll AR::kUnroll
     for (int t = 0; t < nt; ++t) {
       const XE* p = rt.xp[t] + s_node;                     // vertex (cx, cy) of column j
       const T w = AR::template weight<WT>(ldg_ce(rt.wp[t] + e), rt.g[t]);

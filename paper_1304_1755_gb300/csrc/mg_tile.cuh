@@ -158,10 +158,12 @@ __global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict_
 // Pass 1 takes the window of fine nodes Y0-1 .. Y0+MU_FY (rows) x X0-1 .. X0+MU_FX (columns) in
 // 2 x 2 blocks: block (R, C) holds fine nodes (2R+1, 2C+1) on coarse node (R, C), (2R+1, 2C+2),
 // (2R+2, 2C+1) and (2R+2, 2C+2) between it and (R, C+1), (R+1, C), (R+1, C+1), so the bilinear
-// prolongation e = P x_c needs the same four coarse values for all four fine nodes.  It stores
-// g = (c^2/3) b + (c/3) e (zero outside the grid) for the whole window and
-// (2c - 3c^2) b + (1 - 3c) e for the tile's own nodes, in shared memory (arithmetic type).  Pass 2 adds
-// the 3 x 3 box sum of g: a thread owns two fine columns and walks eight rows with the
+// prolongation e = P x_c needs the same four coarse values for all four fine nodes, and stores
+// g = (c^2/3) b + (c/3) e for the whole window in shared memory.  No node needs a test: the
+// windows are zero outside the grid, and a fine node outside it (or on its boundary) only
+// interpolates coarse nodes outside it, so its b, e and g are zero.  Pass 2 adds the 3 x 3 box
+// sum of g to (2c - 3c^2) b + (1 - 3c) e = alpha g + beta b (alpha = (1 - 3c)/(c/3), beta =
+// 2c - 3c^2 - alpha c^2/3): a thread owns two fine columns and walks RW rows with the
 // horizontal three-sums in registers.
 template <typename TB, typename TS, typename TA, typename TO = TS>
 __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ b, const TS* __restrict__ xc,
@@ -170,12 +172,12 @@ __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ 
   constexpr int MU_FY = mu_fy<TB, TS, TA>(), RW = MU_FY / 4;   // tile rows, rows per warp in pass 2
   constexpr int NRB = MU_FY + 2, NCB = MU_FX + 2, SWB = win_pitch<TB, NCB>();
   constexpr int NRC = MU_FY / 2 + 3, NCC = MU_FX / 2 + 3, SWC = win_pitch<TS, NCC>();
-  constexpr int BR = NRB / 2, BC = NCB / 2;      // 2 x 2 blocks of the window
+  constexpr int BR = NRB / 2, BC = NCB / 2;      // 2 x 2 blocks of the window (BC = 65)
+  static_assert(BC == 65 && MT_THREADS == 256, "pass 1 maps 64 block columns x 4 block rows per sweep");
   __shared__ __align__(16) TB sb[NRB * SWB];
   __shared__ __align__(16) TS sc[NRC * SWC];
   __shared__ int phb[NRB], phc[NRC];
   __shared__ TA sg[NRB][NCB];                    // g over the window
-  __shared__ TA se[MU_FY][MU_FX];                // the b, e part of the tile's own nodes
   const int X0 = (blockIdx.x % tiles_x) * MU_FX, Y0 = (blockIdx.x / tiles_x) * MU_FY;
   load_window<TB, NRB, NCB>(b + (size_t)blockIdx.y * ldb, m, Y0 - 1, X0 - 1, sb, phb);
   load_window<TS, NRC, NCC>(xc + (size_t)blockIdx.y * ldc, mc, Y0 / 2 - 1, X0 / 2 - 1, sc, phc);
@@ -184,50 +186,50 @@ __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ 
   const TA cgb = c * c / TA(3), cge = c / TA(3), cbb = TA(2) * c - TA(3) * c * c, cee = TA(1) - TA(3) * c;
   // pass 1: block (br, bc) of the window = coarse node (Y0/2 - 1 + br, X0/2 - 1 + bc) = window
   // coarse row br, column bc; its fine nodes are window rows 2br, 2br+1 and columns 2bc, 2bc+1
-  for (int t = threadIdx.x; t < BR * BC; t += MT_THREADS) {
-    const int br = t / BC, bc = t - br * BC;
+  auto block = [&](int br, int bc) {
     const TS* c0 = sc + br * SWC + phc[br] + bc;
     const TS* c1 = sc + (br + 1) * SWC + phc[br + 1] + bc;
     const TA x00 = sld<TA>(c0), x01 = sld<TA>(c0 + 1), x10 = sld<TA>(c1), x11 = sld<TA>(c1 + 1);
-    const TA e[2][2] = {{x00, TA(0.5) * (x00 + x01)},
-                        {TA(0.5) * (x00 + x10), TA(0.25) * ((x00 + x01) + (x10 + x11))}};
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const int rr = 2 * br + dy;                 // window row; fine row Y0 - 1 + rr
-      const int j = Y0 - 1 + rr;
-      const TB* brow = sb + rr * SWB + phb[rr] + 2 * bc;
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int cw = 2 * bc + dx, i = X0 - 1 + cw;
-        const TA bv = sld<TA>(brow + dx);
-        const bool in = j >= 0 && j < m && i >= 0 && i < m;
-        sg[rr][cw] = in ? cgb * bv + cge * e[dy][dx] : TA(0);
-        if (rr >= 1 && rr <= MU_FY && cw >= 1 && cw <= MU_FX) se[rr - 1][cw - 1] = cbb * bv + cee * e[dy][dx];
-      }
-    }
+    const TA h0 = TA(0.5) * (x00 + x01), v0 = TA(0.5) * (x00 + x10), q = TA(0.25) * ((x00 + x01) + (x10 + x11));
+    const TB* b0 = sb + (2 * br) * SWB + phb[2 * br] + 2 * bc;
+    const TB* b1 = sb + (2 * br + 1) * SWB + phb[2 * br + 1] + 2 * bc;
+    TA* g0 = &sg[2 * br][2 * bc];
+    TA* g1 = &sg[2 * br + 1][2 * bc];
+    g0[0] = cgb * sld<TA>(b0) + cge * x00;
+    g0[1] = cgb * sld<TA>(b0 + 1) + cge * h0;
+    g1[0] = cgb * sld<TA>(b1) + cge * v0;
+    g1[1] = cgb * sld<TA>(b1 + 1) + cge * q;
+  };
+  {
+    const int bc = threadIdx.x & 63;
+    for (int br = threadIdx.x >> 6; br < BR; br += 4) block(br, bc);
+    if (threadIdx.x < BR) block(threadIdx.x, 64);
   }
   __syncthreads();
   // pass 2: thread columns k0, k0 + 1 of the tile, rows jw .. jw + RW - 1
+  const TA alpha = cee / cge, beta = cbb - alpha * cgb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k0 = 64 * (warp & 1) + 2 * lane;
   const int jw = RW * (warp >> 1);
   const int i0 = X0 + k0, i1 = i0 + 1;
-  TA H0[RW + 2], H1[RW + 2];
+  TA H0[RW + 2], H1[RW + 2], G0[RW + 2], G1[RW + 2];
 #pragma unroll
   for (int k = 0; k < RW + 2; ++k) {              // window rows jw .. jw + RW + 1 = fine rows Y0 + jw - 1 ..
     const TA* gr = &sg[jw + k][k0];               // window columns k0 .. k0 + 3 = fine i0 - 1 .. i1 + 1
     const TA gm = gr[0], g0 = gr[1], g1 = gr[2], gp = gr[3];
     H0[k] = (gm + g0) + g1;
     H1[k] = (g0 + g1) + gp;
+    G0[k] = g0, G1[k] = g1;
   }
   TO* xb = x + (size_t)blockIdx.y * ldx;
 #pragma unroll
   for (int q = 0; q < RW; ++q) {
     const int j = Y0 + jw + q;
     if (j < m) {
+      const TB* br = sb + (jw + q + 1) * SWB + phb[jw + q + 1] + k0 + 1;   // b at i0, i1
       TO* op = xb + (size_t)j * m;
-      if (i0 < m) st_as<TO, TA>(op + i0, se[jw + q][k0] + ((H0[q] + H0[q + 1]) + H0[q + 2]));
-      if (i1 < m) st_as<TO, TA>(op + i1, se[jw + q][k0 + 1] + ((H1[q] + H1[q + 1]) + H1[q + 2]));
+      if (i0 < m) st_as<TO, TA>(op + i0, alpha * G0[q + 1] + beta * sld<TA>(br) + ((H0[q] + H0[q + 1]) + H0[q + 2]));
+      if (i1 < m) st_as<TO, TA>(op + i1, alpha * G1[q + 1] + beta * sld<TA>(br + 1) + ((H1[q] + H1[q + 1]) + H1[q + 2]));
     }
   }
 }

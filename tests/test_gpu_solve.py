@@ -82,7 +82,8 @@ def test_c1_iteration_counts_bt_below_bd():
 
 
 @pytest.mark.parametrize("n,M,p,fam,mean", [(65, 3, 3, basis.HERMITE, "lognormal"), (129, 2, 2, basis.LEGENDRE, "one"),
-                                              (17, 1, 0, basis.LEGENDRE, "one"), (5, 6, 4, basis.LEGENDRE, "one")])
+                                              (17, 1, 0, basis.LEGENDRE, "one"), (5, 6, 4, basis.LEGENDRE, "one"),
+                                              (33, 0, 3, basis.LEGENDRE, "lognormal")])
 def test_solves_other_shapes(n, M, p, fam, mean):
     import torch
     pr = Pair(n, M, p, fam, sigma=0.2, mean=mean)
