@@ -43,6 +43,12 @@ WORKLOADS = {
     # vectors of 439 MB (> L2) with about 5 GB on the device, for detailed kernel profiles
     "c3s": dict(n=513, M=6, p=4, family=1, sigma=0.2, restart=4, pc_prec=4, tol=1e-8, f_seed=None,
                 name="sg_c3_copy_513sq_M6_hermite_p4_P210_fgmres4_bf16pc_f32z"),
+    # the paper's own experiment (Table 3) in this discretisation: h = 1/64, m = 6 Legendre, p = 4,
+    # f = 2 (0.5 - x^2 - y^2) on (-0.5, 0.5)^2, sigma 0.1 .. 0.4, tol 1e-10, x0 = 0, two smoothing
+    # steps before and after; the five methods of the table (context: the paper uses P1 triangles and
+    # point Gauss-Seidel)
+    "table3": dict(n=65, M=6, p=4, family=0, sigmas=(0.1, 0.2, 0.3, 0.4), tol=1e-10, restart=10, nu=2,
+                   name="paper_table3_65sq_M6_legendre_p4_tol1e-10"),
     # adjoint gradient of J = E[int u] + Var[int u] / 2 w.r.t. the per-cell mean and sigma.  At sigma =
     # 0.4 the 257^2 system (lognormal mean, not coercive at the xi-box corners) makes restarted
     # GMRES(30) stagnate near 1e-6 in FP64 as well, so the timed gradient uses sigma = 0.3; the
@@ -339,7 +345,11 @@ def run_ours(args, wl, rank, world):
         "peak": round(peak, 2),
         "unit": "TFLOP/s",
         "frac": round(achieved / peak, 4),
-        "traffic": None,
+        # DRAM bytes of one launch from the ncu capture of this kernel on the 513^2 copy of C3
+        # (profiles/k_apply_df_outer_operator_c3s_513sq_P210.md: 272.98 MB read + 391.96 MB written for
+        # 54,835,410 unknowns, 12.13 B per unknown), scaled to this workload's unknowns
+        "traffic": (round(12.126 * h.P * h.Nx) if df and wl["pc_prec"] in (sg.F32, sg.BF16Z) else None),
+        "traffic_unit": "bytes",
         "launch_ms": round(k1_launch_ms, 4),
         "flops_per_launch": fl,
         "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock (FP32 flops of the "
@@ -386,6 +396,65 @@ def c2_sweep(wl, stream):
                              "ms": round(e0.elapsed_time(e1), 3)})
         h.close()
     return rows
+
+
+def run_table3(args, wl, rank, world):
+    """The five methods of the paper's Table 3 (B-GS, BD-PCG, BT-GPCG, BT-GMRes(10), BS-PCG), FP64, on
+    this repository's Q1 / damped-Jacobi V(2,2) discretisation of the paper's test problem; iteration
+    counts and device times, with the paper's counts (P1 triangles, point Gauss-Seidel V(2,2), MATLAB)
+    beside them as context."""
+    import numpy as np
+    import torch
+    from paper_1304_1755_gb300 import build as B
+    from paper_1304_1755_gb300 import sg
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if not os.path.exists(sg.LIB_PATH):
+        B.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    paper = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_examples.json")))["table3"]
+    n, M, p = wl["n"], wl["M"], wl["p"]
+    h1 = 1.0 / (n - 1)
+    xs = np.arange(1, n - 1) * h1 - 0.5                      # interior nodes of (-0.5, 0.5)
+    X, Y = np.meshgrid(xs, xs)
+    f = (2.0 * (0.5 - X ** 2 - Y ** 2)).reshape(-1)
+    unit, _ = sg.sg_kl_coef(n, M, 1.0)
+    methods = [("Block-GS", sg.BGS, sg.PC_BLOCKTRI), ("BD-PCG", sg.PCG, sg.PC_BLOCKDIAG),
+               ("BT-GPCG", sg.GPCG, sg.PC_BLOCKTRI), ("BT-GMRes", sg.GMRES, sg.PC_BLOCKTRI),
+               ("BS-PCG", sg.PCG, sg.PC_BLOCKSYM)]
+    rows, total_ms = [], 0.0
+    for si, sigma in enumerate(wl["sigmas"]):
+        coef = unit.copy()
+        coef[0] = 1.0
+        coef[1:] *= sigma
+        h = sg.Handle(n, M, p, wl["family"], coef, nu1=wl["nu"], nu2=wl["nu"], stream=stream)
+        F = torch.zeros(h.P * h.Nx, dtype=torch.float64, device="cuda")
+        F[:h.Nx] = torch.as_tensor(f * h1 * h1)
+        for name, meth, pc in methods:
+            U = torch.zeros_like(F)
+            o = dict(method=meth, precond=pc, restart=wl["restart"], maxit=1000, tol=wl["tol"], pc_prec=sg.F64,
+                     check=False)
+            h.solve(F, U, **o)
+            U.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            info = h.solve(F, U, **o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            total_ms += ms
+            rows.append({"sigma": sigma, "method": name, "iterations": info.iters, "status": info.status,
+                         "relres_true": info.relres_true, "ms": round(ms, 3),
+                         "paper_iterations": paper[name][si][0], "paper_cpu_s": paper[name][si][1]})
+        h.close()
+    return {"metric": "Table 3 methods on the paper's test problem: iterations and time (context)",
+            "value": round(total_ms / 1e3, 4), "unit": "s (all 20 solves)", "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": round(total_ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (the paper's f and KL setting)",
+            "config": {"workload": wl["name"], "smoother": "damped Jacobi V(2,2)", "elements": "Q1"},
+            "rows": rows, "gpu_launches": None, "e2e": None, "clocks": None, "roofline": None}
 
 
 def c4_cpu_sample(wl, warmup=0, steps=1):
@@ -735,6 +804,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        if args.workload in ("table3", "c3s"):
+            print(json.dumps({"impl": "reference", "unavailable": f"{args.workload} is a context/profiling workload "
+                                                                   "without a reference timing"}))
+            return
         if args.workload == "c4":
             v, sample = c4_cpu_sample(wl, args.warmup, args.steps)
             print(json.dumps({"impl": "reference", "metric": C4_METRIC, "value": round(v, 3), "unit": "s",
@@ -786,6 +859,13 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.workload == "table3":
+        out = run_table3(args, wl, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     if args.workload == "c4":
         out = run_c4(args, wl, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
