@@ -171,7 +171,7 @@ struct OpsF64 {
   double* v(int l) { return V + h->Np * l; }
   void* z(int j) { return (char*)h->kz + prec_size(zprec_of(o.pc_prec)) * h->Np * (flexible ? j : 0); }
   int norm2_rhs(double* out) { int rc; *out = host_dot(h, F, F, N, &rc); return rc; }
-  int zero_solution() { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  int zero_solution() { return vec_fill(h, U, N, 0.0); }
   int residual(bool) { return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F); }
   int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
   int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
@@ -220,7 +220,7 @@ struct OpsDF {
     if ((rc = df_dots(h, nullptr, 0, 0, Fd, h->Np, true))) return rc;
     return copy_red(h, 0, 1, out);
   }
-  int zero_solution() { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  int zero_solution() { return vec_fill(h, U, N, 0.0); }
   int residual(bool u_zero) {
     const size_t Np = h->Np;
     if (u_zero) {
@@ -395,7 +395,7 @@ int solve_gpcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg
   void* gv = h->kz;
   const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
   if (rc) return rc;
-  if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  if (bnorm == 0.0) return vec_fill(h, U, N, 0.0);
   if ((rc = apply_f64(h,0, SG_F64, U, SG_F64, r, F))) return rc;
   double rr = host_dot(h, r, r, N, &rc);
   if (rc) return rc;
@@ -446,7 +446,7 @@ int solve_bgs(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
   const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
   if (rc) return rc;
   if (!std::isfinite(bnorm)) return sg_fail(h, SG_E_NONFINITE, "non-finite right-hand side");
-  if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  if (bnorm == 0.0) return vec_fill(h, U, N, 0.0);
   int its = 0;
   for (;;) {
     if ((rc = apply_f64(h, 0, SG_F64, U, SG_F64, r, F))) return rc;
@@ -476,7 +476,7 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
   void* z = h->kz;
   const double bnorm = std::sqrt(host_dot(h, F, F, N, &rc));
   if (rc) return rc;
-  if (bnorm == 0.0) { SG_CUDA(h, cudaMemsetAsync(U, 0, sizeof(double) * N, h->stream)); return SG_OK; }
+  if (bnorm == 0.0) return vec_fill(h, U, N, 0.0);
   if ((rc = apply_f64(h,0, SG_F64, U, SG_F64, r, F))) return rc;
   if ((rc = apply_precond(h, o.precond, SG_F64, r, z, pcm, o.transpose))) return rc;
   if ((rc = vec_cast(h, zp, z, SG_F64, d, N))) return rc;
@@ -518,8 +518,8 @@ void destroy_ctx(sg_ctx* h) {
   free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off), free_terms(h->t_diag);
   for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
   for (auto& W : h->work) {
-    cudaFree(W.T), cudaFree(W.T32), cudaFree(W.S1), cudaFree(W.S2);
-    for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(W.b[l]), cudaFree(W.x[l]);
+    sg_gfree(W.T), sg_gfree(W.T32), cudaFree(W.S1), cudaFree(W.S2);
+    for (int l = 0; l < SG_MAX_LEVELS; ++l) sg_gfree(W.b[l]), sg_gfree(W.x[l]);
   }
   cudaFree(h->red_partial), cudaFree(h->red_out), cudaFree(h->red_count), cudaFreeHost(h->red_host);
   cudaFree(h->kv), cudaFree(h->kz), cudaFree(h->ktmp), cudaFree(h->dstage);

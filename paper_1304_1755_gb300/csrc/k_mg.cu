@@ -151,12 +151,15 @@ template <> const double* stencil_ptr<double>(const sg_ctx* h, int l) { return h
 template <> const float* stencil_ptr<float>(const sg_ctx* h, int l) { return h->lev[l].st32; }
 
 template <typename TB, typename TS, typename TA>
-int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
+int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc, bool bguard = false) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1) {
     const int tx = (C.m + MD_TX - 1) / MD_TX, ty = (C.m + MD_TY - 1) / MD_TY;
-    mg_down_tile<TB, TS, TA><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, bc, F.m, C.m, F.N, C.N,
-                                                                            (TA)(h->omega * 3.0 / 8.0), tx);
+    const TA c = (TA)(h->omega * 3.0 / 8.0);
+    if (bguard)
+      mg_down_tile<TB, TS, TA, true><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, bc, F.m, C.m, F.N, C.N, c, tx);
+    else
+      mg_down_tile<TB, TS, TA, false><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, bc, F.m, C.m, F.N, C.N, c, tx);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;
@@ -174,13 +177,19 @@ int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc) {
 }
 
 template <typename TB, typename TS, typename TA, typename TO = TS>
-int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TO* x) {
+int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TO* x, bool bguard = false, bool cguard = false) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1 && h->nu2 == 1) {
     constexpr int FY = mu_fy<TB, TS, TA>();
     const int tx = (F.m + MU_FX - 1) / MU_FX, ty = (F.m + FY - 1) / FY;
-    mg_up_tile<TB, TS, TA, TO><<<dim3(tx * ty, nb), MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N,
-                                                                          (TA)(h->omega * 3.0 / 8.0), tx);
+    const dim3 grid(tx * ty, nb);
+    const TA c = (TA)(h->omega * 3.0 / 8.0);
+    if (bguard && cguard)
+      mg_up_tile<TB, TS, TA, TO, true, true><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx);
+    else if (cguard)
+      mg_up_tile<TB, TS, TA, TO, false, true><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx);
+    else
+      mg_up_tile<TB, TS, TA, TO, false, false><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;
@@ -226,27 +235,42 @@ int run_coarse(sg_ctx* h, int nb, const TB* b, TO* x) {
   return SG_OK;
 }
 
+// bguard: B lies in a guarded buffer; lguard: the level buffers of W are guarded (the handle's
+// workspace is, the static scratch of sg_vcycle_static is not).
 template <typename TB, typename TS, typename TA, typename TO = TS>
-int vcycle_t(sg_ctx* h, int nb, const TB* B, TO* X, PrecWork& W) {
+int vcycle_t(sg_ctx* h, int nb, const TB* B, TO* X, PrecWork& W, bool bguard = false, bool lguard = false) {
   int rc;
   const int lc = h->lc;
   // descend
   for (int l = 0; l < lc; ++l) {
-    if (l == 0) rc = run_down<TB, TS, TA>(h, 0, nb, B, (TS*)W.b[1]);
-    else rc = run_down<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (TS*)W.b[l + 1]);
+    if (l == 0) rc = run_down<TB, TS, TA>(h, 0, nb, B, (TS*)W.b[1], bguard);
+    else rc = run_down<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (TS*)W.b[l + 1], lguard);
     if (rc) return rc;
   }
   if (lc == 0) rc = run_coarse<TB, TS, TA, TO>(h, nb, B, X);
   else rc = run_coarse<TS, TS, TA>(h, nb, (const TS*)W.b[lc], (TS*)W.x[lc]);
   if (rc) return rc;
   for (int l = lc - 1; l >= 0; --l) {
-    if (l == 0) rc = run_up<TB, TS, TA, TO>(h, 0, nb, B, (const TS*)W.x[1], X);
-    else rc = run_up<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (const TS*)W.x[l + 1], (TS*)W.x[l]);
+    if (l == 0) rc = run_up<TB, TS, TA, TO>(h, 0, nb, B, (const TS*)W.x[1], X, bguard, lguard);
+    else rc = run_up<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (const TS*)W.x[l + 1], (TS*)W.x[l], lguard, lguard);
     if (rc) return rc;
   }
   return SG_OK;
 }
+
+// Buffers that the tile loaders may over-fetch around: 256 bytes before and 4 KB after the data
+// (more than the widest window row), so whole aligned 16-byte chunks never leave the allocation.
+constexpr size_t GUARD_FRONT = 256, GUARD_BACK = 4096;
 }  // namespace
+
+void* sg_galloc(size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes + GUARD_FRONT + GUARD_BACK) != cudaSuccess) return nullptr;
+  return (char*)p + GUARD_FRONT;
+}
+void sg_gfree(void* p) {
+  if (p) cudaFree((char*)p - GUARD_FRONT);
+}
 
 int ensure_prec_work(sg_ctx* h, int mode) {
   const int prec = wprec_of(mode);
@@ -254,45 +278,45 @@ int ensure_prec_work(sg_ctx* h, int mode) {
   if (mode == SG_BF16Z && !W.T32) {
     int nqmax = 0;
     for (int q = 0; q <= h->p; ++q) nqmax = std::max(nqmax, h->lvl_off[q + 1] - h->lvl_off[q]);
-    if (cudaMalloc(&W.T32, sizeof(float) * (size_t)nqmax * h->Nx) != cudaSuccess)
+    if (!(W.T32 = sg_galloc(sizeof(float) * (size_t)nqmax * h->Nx)))
       return sg_fail(h, SG_E_ALLOC, "alloc FP32 stage buffer");
   }
   if (W.ready) return SG_OK;
   const size_t es = prec_size(prec);
   int nqmax = 0;
   for (int q = 0; q <= h->p; ++q) nqmax = std::max(nqmax, h->lvl_off[q + 1] - h->lvl_off[q]);
-  if (cudaMalloc(&W.T, es * (size_t)nqmax * h->Nx) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc stage buffer");
+  if (!(W.T = sg_galloc(es * (size_t)nqmax * h->Nx))) return sg_fail(h, SG_E_ALLOC, "alloc stage buffer");
   for (int l = 1; l < h->nlev; ++l) {
     const size_t bytes = es * (size_t)h->P * h->lev[l].N;
-    if (cudaMalloc(&W.b[l], bytes) != cudaSuccess || cudaMalloc(&W.x[l], bytes) != cudaSuccess)
+    if (!(W.b[l] = sg_galloc(bytes)) || !(W.x[l] = sg_galloc(bytes)))
       return sg_fail(h, SG_E_ALLOC, "alloc multigrid level");
   }
   W.ready = true;
   return SG_OK;
 }
 
-int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X) {
+int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard) {
   if (nb <= 0) return SG_OK;
   if (nb > h->P) return sg_fail(h, SG_E_ARG, "vcycle: more blocks than the workspace holds");
   int rc = ensure_prec_work(h, prec);
   if (rc) return rc;
   PrecWork& W = h->work[wprec_of(prec)];
   if (prec == SG_BF16Z) {                 // BF16 levels, FP32 output
-    if (bprec == SG_F64) return vcycle_t<double, bf16, float, float>(h, nb, (const double*)B, (float*)X, W);
-    if (bprec == SG_F32) return vcycle_t<float, bf16, float, float>(h, nb, (const float*)B, (float*)X, W);
-    return vcycle_t<bf16, bf16, float, float>(h, nb, (const bf16*)B, (float*)X, W);
+    if (bprec == SG_F64) return vcycle_t<double, bf16, float, float>(h, nb, (const double*)B, (float*)X, W, bguard, true);
+    if (bprec == SG_F32) return vcycle_t<float, bf16, float, float>(h, nb, (const float*)B, (float*)X, W, bguard, true);
+    return vcycle_t<bf16, bf16, float, float>(h, nb, (const bf16*)B, (float*)X, W, bguard, true);
   }
   if (prec == SG_F64) {
     if (bprec != SG_F64) return sg_fail(h, SG_E_ARG, "vcycle: FP64 cycle needs FP64 input");
-    return vcycle_t<double, double, double>(h, nb, (const double*)B, (double*)X, W);
+    return vcycle_t<double, double, double>(h, nb, (const double*)B, (double*)X, W, bguard, true);
   }
   if (prec == SG_F32) {
-    if (bprec == SG_F64) return vcycle_t<double, float, float>(h, nb, (const double*)B, (float*)X, W);
-    return vcycle_t<float, float, float>(h, nb, (const float*)B, (float*)X, W);
+    if (bprec == SG_F64) return vcycle_t<double, float, float>(h, nb, (const double*)B, (float*)X, W, bguard, true);
+    return vcycle_t<float, float, float>(h, nb, (const float*)B, (float*)X, W, bguard, true);
   }
-  if (bprec == SG_F64) return vcycle_t<double, bf16, float>(h, nb, (const double*)B, (bf16*)X, W);
-  if (bprec == SG_F32) return vcycle_t<float, bf16, float>(h, nb, (const float*)B, (bf16*)X, W);
-  return vcycle_t<bf16, bf16, float>(h, nb, (const bf16*)B, (bf16*)X, W);
+  if (bprec == SG_F64) return vcycle_t<double, bf16, float>(h, nb, (const double*)B, (bf16*)X, W, bguard, true);
+  if (bprec == SG_F32) return vcycle_t<float, bf16, float>(h, nb, (const float*)B, (bf16*)X, W, bguard, true);
+  return vcycle_t<bf16, bf16, float>(h, nb, (const bf16*)B, (bf16*)X, W, bguard, true);
 }
 
 // A preconditioner application is a fixed sequence of about ten launches per degree
@@ -350,13 +374,13 @@ static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z,
     const int r0 = h->lvl_off[q], nq = h->lvl_off[q + 1] - r0;
     char* Zq = (char*)Z + es * (size_t)r0 * h->Nx;
     if (s == 0) {
-      rc = vcycle_run(h, prec, nq, (const char*)R + rs * (size_t)r0 * h->Nx, rprec, Zq);
+      rc = vcycle_run(h, prec, nq, (const char*)R + rs * (size_t)r0 * h->Nx, rprec, Zq, false);
     } else {
       // T_q = R_q - sum over the couplings to the previous stage of G_k(i,j) K_k Z_j
       void* T = prec == SG_BF16Z ? h->work[wp].T32 : h->work[wp].T;
       rc = launch_apply(h, transpose ? 2 : 1, zp, Z, 0, tp, T, 0, rprec, R, 0, r0, nq, r0, 0, arith);
       if (rc) return rc;
-      rc = vcycle_run(h, prec, nq, T, tp, Zq);
+      rc = vcycle_run(h, prec, nq, T, tp, Zq, true);
     }
     if (rc) return rc;
   }

@@ -210,6 +210,10 @@ __global__ void k_update_df(float* __restrict__ U, const TZ* __restrict__ Z, siz
   }
 }
 
+__global__ void k_fill(double* __restrict__ y, size_t N, double v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) y[i] = v;
+}
+
 // split an FP64 vector into a double-float vector; positions [N, lo) of both halves are zeroed
 // (the padding of Krylov vectors must stay zero)
 __global__ void k_df_from_f64(const double* __restrict__ x, float* __restrict__ y, size_t N, size_t lo) {
@@ -456,6 +460,13 @@ int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t l
   count_launch(h);
   // the host staging slot is reused by the next call: wait for this copy
   SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SG_OK;
+}
+
+int vec_fill(sg_ctx* h, double* y, size_t N, double v) {
+  k_fill<<<grid_for(N), 256, 0, h->stream>>>(y, N, v);
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
   return SG_OK;
 }
 

@@ -52,13 +52,33 @@ template <typename T, int NC> constexpr int win_pitch() {
 // warp, warp + 8, ...: the 16-byte aligned middle of a row goes by cp.async, the up to
 // 2 (V - 1) ragged end elements by plain loads that are all issued before any of them is
 // stored, so a warp waits for one memory latency, not one per row.
-template <typename T, int NR, int NC>
+template <typename T, int NR, int NC, bool OVER = false>
 __device__ __forceinline__ void load_window(const T* __restrict__ g, int m, int r0, int c0, T* sw, int* sph) {
   constexpr int V = 16 / (int)sizeof(T);
   constexpr int SW = win_pitch<T, NC>();
   constexpr int NW = MT_THREADS / 32;
   constexpr int RPW = (NR + NW - 1) / NW;               // rows per warp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (OVER) {
+    // guarded array: copy whole aligned 16-byte chunks around every row segment; the bytes outside
+    // the segment land in the row's slack or in columns fix_window_columns() zeroes afterwards
+    for (int rr = warp; rr < NR; rr += NW) {
+      const int r = r0 + rr;
+      T* srow = sw + rr * SW;
+      if (r < 0 || r >= m) {
+        for (int k = lane; k < NC; k += 32) srow[k] = zero_of<T>();
+        if (lane == 0) sph[rr] = 0;
+        continue;
+      }
+      const uintptr_t a0 = (uintptr_t)(g + (size_t)r * m) + (uintptr_t)((intptr_t)c0 * (intptr_t)sizeof(T));
+      const int ph = (int)((a0 & 15u) / sizeof(T));
+      if (lane == 0) sph[rr] = ph;
+      const char* src = (const char*)(a0 & ~(uintptr_t)15);
+      const int nch = (ph + NC + V - 1) / V;            // <= NCH
+      for (int q = lane; q < nch; q += 32) cp_async16((char*)srow + 16 * q, src + 16 * q);
+    }
+    return;
+  }
   T endv[RPW];
   int endk[RPW];                                        // window column of this lane's end element, or -1
 #pragma unroll
@@ -112,22 +132,41 @@ __device__ __forceinline__ void load_window(const T* __restrict__ g, int m, int 
   }
 }
 
+// After an over-fetching load_window has landed and the CTA has synchronised: zero the window
+// columns outside [0, m) (only tiles at the left or right edge of the grid have any) and
+// synchronise again if anything was written.
+template <typename T, int NR, int NC>
+__device__ __forceinline__ void fix_window_columns(T* sw, const int* sph, int c0, int m) {
+  constexpr int SW = win_pitch<T, NC>();
+  if (c0 >= 0 && c0 + NC <= m) return;                  // uniform over the CTA
+  const int zl = max(0, min(NC, -c0)), zr = max(0, min(NC, c0 + NC - m));
+  for (int t = threadIdx.x; t < NR * 32; t += MT_THREADS) {
+    const int rr = t >> 5, k = t & 31;
+    T* sbase = sw + rr * SW + sph[rr];
+    for (int q = k; q < zl; q += 32) sbase[q] = zero_of<T>();
+    for (int q = k; q < zr; q += 32) sbase[NC - 1 - q] = zero_of<T>();
+  }
+  __syncthreads();
+}
+
 template <typename TA, typename T> __device__ __forceinline__ TA sld(const T* p) { return ld_as<TA>(p); }
 
 // ---------------------------------------------------------------------------
 // down: tile of MD_TX x MD_TY coarse nodes; fine window rows 2J0-1 .. 2J0+2MD_TY+1,
 // columns 2I0-1 .. 2I0+2MD_TX+1.  Warp w: coarse columns 32 (w & 1) + lane, coarse rows
 // 4 (w >> 1) .. +3.
-template <typename TB, typename TS, typename TA>
+// OB: b lies in a guarded array (load_window may over-fetch aligned chunks).
+template <typename TB, typename TS, typename TA, bool OB = false>
 __global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict__ b, TS* __restrict__ bc, int m,
                                                            int mc, size_t ldb, size_t ldc, TA c, int tiles_x) {
   constexpr int NR = 2 * MD_TY + 3, NC = 2 * MD_TX + 3, SW = win_pitch<TB, NC>();
   __shared__ __align__(16) TB sw[NR * SW];
   __shared__ int sph[NR];
   const int I0 = (blockIdx.x % tiles_x) * MD_TX, J0 = (blockIdx.x / tiles_x) * MD_TY;
-  load_window<TB, NR, NC>(b + (size_t)blockIdx.y * ldb, m, 2 * J0 - 1, 2 * I0 - 1, sw, sph);
+  load_window<TB, NR, NC, OB>(b + (size_t)blockIdx.y * ldb, m, 2 * J0 - 1, 2 * I0 - 1, sw, sph);
   cp_async_wait_all();
   __syncthreads();
+  if (OB) fix_window_columns<TB, NR, NC>(sw, sph, 2 * I0 - 1, m);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = 32 * (warp & 1) + lane;           // coarse column within the tile
   const int jw = 4 * (warp >> 1);                 // first coarse row of this warp
@@ -165,7 +204,8 @@ __global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict_
 // sum of g to (2c - 3c^2) b + (1 - 3c) e = alpha g + beta b (alpha = (1 - 3c)/(c/3), beta =
 // 2c - 3c^2 - alpha c^2/3): a thread owns two fine columns and walks RW rows with the
 // horizontal three-sums in registers.
-template <typename TB, typename TS, typename TA, typename TO = TS>
+// OB, OC: b, x_c lie in guarded arrays (load_window may over-fetch aligned chunks).
+template <typename TB, typename TS, typename TA, typename TO = TS, bool OB = false, bool OC = false>
 __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ b, const TS* __restrict__ xc,
                                                          TO* __restrict__ x, int m, int mc, size_t ldb, size_t ldc,
                                                          size_t ldx, TA c, int tiles_x) {
@@ -179,10 +219,12 @@ __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ 
   __shared__ int phb[NRB], phc[NRC];
   __shared__ TA sg[NRB][NCB];                    // g over the window
   const int X0 = (blockIdx.x % tiles_x) * MU_FX, Y0 = (blockIdx.x / tiles_x) * MU_FY;
-  load_window<TB, NRB, NCB>(b + (size_t)blockIdx.y * ldb, m, Y0 - 1, X0 - 1, sb, phb);
-  load_window<TS, NRC, NCC>(xc + (size_t)blockIdx.y * ldc, mc, Y0 / 2 - 1, X0 / 2 - 1, sc, phc);
+  load_window<TB, NRB, NCB, OB>(b + (size_t)blockIdx.y * ldb, m, Y0 - 1, X0 - 1, sb, phb);
+  load_window<TS, NRC, NCC, OC>(xc + (size_t)blockIdx.y * ldc, mc, Y0 / 2 - 1, X0 / 2 - 1, sc, phc);
   cp_async_wait_all();
   __syncthreads();
+  if (OB) fix_window_columns<TB, NRB, NCB>(sb, phb, X0 - 1, m);
+  if (OC) fix_window_columns<TS, NRC, NCC>(sc, phc, X0 / 2 - 1, mc);
   const TA cgb = c * c / TA(3), cge = c / TA(3), cbb = TA(2) * c - TA(3) * c * c, cee = TA(1) - TA(3) * c;
   // pass 1: block (br, bc) of the window = coarse node (Y0/2 - 1 + br, X0/2 - 1 + bc) = window
   // coarse row br, column bc; its fine nodes are window rows 2br, 2br+1 and columns 2bc, 2bc+1

@@ -185,7 +185,11 @@ int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int
                  int rprec, const void* R, size_t rlo, int row0, int nrows, int ybase, int rbase, int arith);
 
 // k_mg.cu
-int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X);
+// bguard: B lies in a guarded buffer (sg_galloc), so the tile loaders may over-fetch around it
+int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard = false);
+// device buffers with 256 bytes before and 4 KB after the data, for the multigrid tile loaders
+void* sg_galloc(size_t bytes);
+void sg_gfree(void* p);
 int ensure_prec_work(sg_ctx* h, int prec);
 // R is FP64 (rprec SG_F64) or FP32 (rprec SG_F32, e.g. the hi array of a double-float vector)
 int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose);
@@ -199,6 +203,7 @@ int vec_axpys_norm(sg_ctx* h, const double* V, size_t ldv, int nv, const double*
 int vec_update(sg_ctx* h, double* U, int zprec, const void* Z, size_t ldz, int nz, const double* y_host, size_t N);
 int vec_cast(sg_ctx* h, int iprec, const void* in, int oprec, void* out, size_t N);
 int vec_axpby(sg_ctx* h, double a, const double* x, double b, double* y, size_t N);   // y = a x + b y
+int vec_fill(sg_ctx* h, double* y, size_t N, double v);    // by a kernel (also for mapped host memory)
 int vec_dot_pairs(sg_ctx* h, int npairs, const double* const* xs, const void* const* ys, const int* yprecs,
                   size_t N, double* out_host);
 int vec_axpy_prec(sg_ctx* h, double a, int xprec, const void* x, double* y, size_t N);  // y += a x

@@ -180,3 +180,19 @@ def test_switching_krylov_arithmetic_on_one_handle():
         assert info.status == 0 and info.relres_true <= 1e-10
         got = host(U)
         assert np.linalg.norm(got - Ustar) <= 1e-6 * np.linalg.norm(Ustar)
+
+
+def test_pinned_host_buffers_solve():
+    """Page-locked host F and U give the device solve's answer."""
+    import torch
+    pr = Pair(65, 2, 3, sigma=0.3)
+    F = osg.rhs(pr.sys)
+    opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=20, tol=1e-10, pc_prec=sg.F32, arith=sg.ARITH_DF64)
+    Ud = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
+    pr.h.solve(dev(F), Ud, **opts)
+    Fh = torch.as_tensor(F).pin_memory()
+    Uh = torch.full((pr.N,), 7.0, dtype=torch.float64).pin_memory()
+    info = pr.h.solve(Fh, Uh, **opts)
+    torch.cuda.synchronize()
+    assert info.status == 0 and info.relres_true <= 1e-10
+    assert np.abs(Uh.numpy() - host(Ud)).max() <= 1e-14 * np.abs(host(Ud)).max()
