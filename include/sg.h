@@ -197,8 +197,11 @@ int sg_vcycle_static(sg_handle h, const double* B, void* X, int nblocks, int pre
 
 /* Solve A U = F (or A^T U = F).  F, U: FP64, host or device pointers (host
  * buffers are staged through device memory inside the call; page-locked ones copy
- * fastest).  info may be NULL.  Returns SG_E_NOCONV if maxit is reached (U then
- * holds the last iterate). */
+ * fastest, and for GMRES/FGMRES a page-locked U receives each restart's iterate on a
+ * side stream while its true residual is checked, so the converged solution is already
+ * on the host when the check confirms it).  info may be NULL.  Returns SG_E_NOCONV if
+ * maxit is reached (U then holds the last iterate).  U is complete when the call
+ * returns. */
 int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info);
 
 /* Solve nsys independent systems, each with its own handle (any mix of grids, M and p;

@@ -96,6 +96,40 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// page-locked host memory (an asynchronous copy into pageable memory would block the host)
+bool is_pinned_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// early copy of the current iterate U (device, N doubles) to h->spec_dst, on the side stream
+int spec_copy_u(sg_ctx* h, const double* U, size_t N) {
+  if (!h->spec_dst) return SG_OK;
+  if (!h->cstream) {
+    SG_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    SG_CUDA(h, cudaEventCreateWithFlags(&h->ev_u, cudaEventDisableTiming));
+    SG_CUDA(h, cudaEventCreateWithFlags(&h->ev_c, cudaEventDisableTiming));
+  }
+  SG_CUDA(h, cudaEventRecord(h->ev_u, h->stream));
+  SG_CUDA(h, cudaStreamWaitEvent(h->cstream, h->ev_u, 0));
+  SG_CUDA(h, cudaMemcpyAsync(h->spec_dst, U, sizeof(double) * N, cudaMemcpyDeviceToHost, h->cstream));
+  SG_CUDA(h, cudaEventRecord(h->ev_c, h->cstream));
+  h->spec_pending = true;
+  return SG_OK;
+}
+
+// before U changes: make the main stream wait for an early copy still reading it
+int spec_invalidate(sg_ctx* h) {
+  if (!h->spec_pending) return SG_OK;
+  SG_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_c, 0));
+  h->spec_pending = false;
+  return SG_OK;
+}
+
 double host_dot(sg_ctx* h, const double* x, const double* y, size_t N, int* rc) {
   const double* xs[1] = {x};
   const void* ys[1] = {y};
@@ -172,13 +206,19 @@ struct OpsF64 {
   void* z(int j) { return (char*)h->kz + prec_size(zprec_of(o.pc_prec)) * h->Np * (flexible ? j : 0); }
   int norm2_rhs(double* out) { int rc; *out = host_dot(h, F, F, N, &rc); return rc; }
   int zero_solution() { return vec_fill(h, U, N, 0.0); }
-  int residual(bool) { return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F); }
+  int residual(bool u_zero) {
+    int rc;
+    if (!u_zero && (rc = spec_copy_u(h, U, N))) return rc;      // U is final if this check converges
+    return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F);
+  }
   int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
   int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
   int apply(int j) { return apply_f64(h, 0, zprec_of(o.pc_prec), z(j), SG_F64, v(j + 1), nullptr); }
   int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
   int axpys(int j, const double* c) { return vec_axpys_norm(h, V, h->Np, j + 1, c, v(j + 1), h->Np, nullptr); }
   int update(int k, const double* y) {
+    int rc0 = spec_invalidate(h);
+    if (rc0) return rc0;
     if (flexible) return vec_update(h, U, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N);
     double* t = h->ktmp;
     SG_CUDA(h, cudaMemsetAsync(t, 0, sizeof(double) * N, h->stream));
@@ -230,7 +270,9 @@ struct OpsDF {
     // restart (and final check): the true residual of the FP64 iterate in IEEE FP64, then split
     int rc;
     double* r64 = h->ktmp + 2 * Np;
+    if ((rc = spec_invalidate(h))) return rc;
     if ((rc = df_to_f64(h, Ud, U, N, Np))) return rc;
+    if ((rc = spec_copy_u(h, U, N))) return rc;                // U is final if this check converges
     if ((rc = apply_f64(h, 0, SG_F64, U, SG_F64, r64, F))) return rc;
     return df_from_f64(h, r64, v(0), N, Np);
   }
@@ -247,7 +289,11 @@ struct OpsDF {
   int dots(int j, bool ww) { return df_dots(h, V, 2 * h->Np, j + 1, v(j + 1), h->Np, ww); }
   int axpys(int j, const double* c) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, c, v(j + 1), h->Np); }
   int update(int k, const double* y) { return df_update(h, Ud, h->Np, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N); }
-  int finish() { return df_to_f64(h, Ud, U, N, h->Np); }
+  int finish() {
+    if (h->true_res_valid) return SG_OK;       // the converged check already wrote this iterate to U
+    int rc = spec_invalidate(h);
+    return rc ? rc : df_to_f64(h, Ud, U, N, h->Np);
+  }
 };
 
 // The basis is normalised lazily: the stored vector l is v_l / s_l with s_l = 1 / ||stored
@@ -523,6 +569,9 @@ void destroy_ctx(sg_ctx* h) {
   }
   cudaFree(h->red_partial), cudaFree(h->red_out), cudaFree(h->red_count), cudaFreeHost(h->red_host);
   cudaFree(h->kv), cudaFree(h->kz), cudaFree(h->ktmp), cudaFree(h->dstage);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
+  if (h->ev_u) cudaEventDestroy(h->ev_u);
+  if (h->ev_c) cudaEventDestroy(h->ev_c);
   delete h;
 }
 }  // namespace
@@ -703,7 +752,11 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
   const bool dev = is_device_ptr(F) && is_device_ptr(U);
   const double* dF = F;
   double* dU = U;
+  h->spec_dst = nullptr;
+  h->spec_pending = false;
   if (!dev) {
+    // FGMRES/GMRES copy the iterate early into page-locked U (overlapping the final residual check)
+    if ((o.method == SG_GMRES || o.method == SG_FGMRES) && is_pinned_host(U)) h->spec_dst = U;
     if (!h->dstage && cudaMalloc(&h->dstage, sizeof(double) * N * 2) != cudaSuccess)
       return sg_fail(h, SG_E_ALLOC, "sg_solve: staging allocation");
     SG_CUDA(h, cudaMemcpyAsync(h->dstage, F, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
@@ -732,8 +785,20 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
     if (rc2) rc = rc2;
     else info.relres_true = ff > 0 ? std::sqrt(rr / ff) : 0.0;
   }
-  if (!dev && (rc == SG_OK || rc == SG_E_NOCONV))
-    SG_CUDA(h, cudaMemcpyAsync(U, dU, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  if (!dev && (rc == SG_OK || rc == SG_E_NOCONV)) {
+    if (rc == SG_OK && h->true_res_valid && h->spec_pending) {
+      // the early copy holds the converged iterate: wait for it instead of copying again
+      SG_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_c, 0));
+    } else {
+      int rc3 = spec_invalidate(h);
+      if (rc3) return rc3;
+      SG_CUDA(h, cudaMemcpyAsync(U, dU, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+    }
+  } else if (h->spec_pending) {
+    SG_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_c, 0));   // no copy in flight past the call
+  }
+  h->spec_dst = nullptr;
+  h->spec_pending = false;
   SG_CUDA(h, cudaEventRecord(e1, h->stream));
   SG_CUDA(h, cudaEventSynchronize(e1));
   float ms = 0;

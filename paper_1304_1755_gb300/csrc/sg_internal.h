@@ -109,6 +109,12 @@ struct sg_ctx {
   Tracer tr;
   int phase = 3;
   bool true_res_valid = false;          // the solver already computed the final FP64 true residual
+  // Host-buffer solves: the iterate is copied to the caller's U on a side stream while its true
+  // residual is being checked, since the check usually confirms convergence.
+  double* spec_dst = nullptr;           // host destination of U (null: no early copy)
+  cudaStream_t cstream = nullptr;       // side stream of the early copy
+  cudaEvent_t ev_u = nullptr, ev_c = nullptr;   // U ready / copy done
+  bool spec_pending = false;            // an early copy was issued and U has not changed since
   int apply_strip[3] = {0, 0, 0};       // operator kernel strip height per arithmetic (FP64, FP32, DF); 0 = default
   // CUDA graphs of whole preconditioner applications, keyed by their operands
   struct GraphEntry {

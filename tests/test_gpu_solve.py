@@ -182,17 +182,32 @@ def test_switching_krylov_arithmetic_on_one_handle():
         assert np.linalg.norm(got - Ustar) <= 1e-6 * np.linalg.norm(Ustar)
 
 
-def test_pinned_host_buffers_solve():
-    """Page-locked host F and U give the device solve's answer."""
+@pytest.mark.parametrize("case", ["df", "f64", "df_noconv", "f64_noconv", "df_x0"])
+def test_pinned_host_buffers_solve(case):
+    """Page-locked host F and U give the device solve's answer, bit for bit: converged (the
+    iterate is copied out while its true residual is checked), stopped at maxit (the early
+    copies of earlier restarts are superseded), and from a given initial guess."""
     import torch
     pr = Pair(65, 2, 3, sigma=0.3)
     F = osg.rhs(pr.sys)
-    opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=20, tol=1e-10, pc_prec=sg.F32, arith=sg.ARITH_DF64)
-    Ud = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
-    pr.h.solve(dev(F), Ud, **opts)
+    opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=5, tol=1e-10, pc_prec=sg.F32, arith=sg.ARITH_DF64)
+    if case.startswith("f64"):
+        opts.update(pc_prec=sg.F64, arith=sg.ARITH_F64, method=sg.GMRES)
+    if case.endswith("noconv"):
+        opts.update(maxit=12)
+    x0 = inputs.uniform(5, pr.N) if case == "df_x0" else None
+    if x0 is not None:
+        opts.update(x0_given=1)
+    Ud = torch.zeros(pr.N, dtype=torch.float64, device="cuda") if x0 is None else dev(x0)
+    opts.update(check=False)
+    info_d = pr.h.solve(dev(F), Ud, **opts)
     Fh = torch.as_tensor(F).pin_memory()
-    Uh = torch.full((pr.N,), 7.0, dtype=torch.float64).pin_memory()
+    Uh = (torch.full((pr.N,), 7.0, dtype=torch.float64) if x0 is None else torch.as_tensor(x0.copy())).pin_memory()
     info = pr.h.solve(Fh, Uh, **opts)
     torch.cuda.synchronize()
-    assert info.status == 0 and info.relres_true <= 1e-10
-    assert np.abs(Uh.numpy() - host(Ud)).max() <= 1e-14 * np.abs(host(Ud)).max()
+    assert info.status == info_d.status and info.iters == info_d.iters
+    if case.endswith("noconv"):
+        assert info.status == -4                                  # SG_E_NOCONV
+    else:
+        assert info.status == 0 and info.relres_true <= 1e-10
+    assert np.array_equal(Uh.numpy(), host(Ud))
