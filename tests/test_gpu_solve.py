@@ -211,3 +211,20 @@ def test_pinned_host_buffers_solve(case):
     else:
         assert info.status == 0 and info.relres_true <= 1e-10
     assert np.array_equal(Uh.numpy(), host(Ud))
+
+
+def test_df_fgmres_long_arnoldi_cycles():
+    """Double-float FGMRES(30) without a preconditioner: Arnoldi cycles of more than 16 steps (the
+    multi-dot and multi-axpy kernels at large basis sizes).  The solve must converge (A is SPD, so
+    restarted GMRES does) and match the direct solution to kappa(A) x tol."""
+    import torch
+    pr = Pair(33, 2, 2, sigma=0.3)
+    F = dev(osg.rhs(pr.sys))
+    Ustar = _direct(pr, host(F))
+    U = torch.zeros_like(F)
+    info = pr.h.solve(F, U, method=sg.FGMRES, precond=sg.PC_NONE, restart=30, maxit=5000, tol=1e-10,
+                      pc_prec=sg.F32, arith=sg.ARITH_DF64)
+    torch.cuda.synchronize()
+    assert info.status == 0 and info.relres_true <= 1e-10
+    assert info.iters > 16
+    assert np.linalg.norm(host(U) - Ustar) <= 1e-6 * np.linalg.norm(Ustar)
