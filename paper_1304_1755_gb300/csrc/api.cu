@@ -56,10 +56,23 @@ int upload_terms(sg_ctx* h, TermTable& T, int which) {
   return SG_OK;
 }
 
-// Double-float weight table W[slot][e] = c_k(e) gamma(n) (slot 0: c_0), when it fits in 2 GB.
+// Weight tables W[slot][e] = c_k(e) gamma(n) (slot 0: c_0) in double-float and in FP64, each when
+// it fits in 2 GB: the operator then reads the product of a term instead of forming it.
 int upload_weights(sg_ctx* h) {
   const size_t slots = 1 + (size_t)h->M * h->p;
   if (slots * h->Nc * 8 > (size_t)2 << 30) return SG_OK;
+  {
+    std::vector<double> w(slots * h->Nc);
+    std::copy(h->coef_h.begin(), h->coef_h.begin() + h->Nc, w.begin());
+    for (int k = 1; k <= h->M; ++k)
+      for (int nn = 0; nn < h->p; ++nn) {
+        const size_t s = 1 + (size_t)(k - 1) * h->p + nn;
+        const double gm = gamma_1d(h->family, nn);
+        for (size_t e = 0; e < h->Nc; ++e) w[s * h->Nc + e] = h->coef_h[(size_t)k * h->Nc + e] * gm;
+      }
+    const int rc = upload(h, &h->w64, w.data(), w.size());
+    if (rc) return rc;
+  }
   std::vector<float> w(2 * slots * h->Nc);
   for (size_t e = 0; e < h->Nc; ++e) {
     const df2 d = df_from_double(h->coef_h[e]);
@@ -560,7 +573,7 @@ void destroy_ctx(sg_ctx* h) {
   if (!h) return;
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
-  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->pvec);
+  cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->w64), cudaFree(h->pvec);
   free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off), free_terms(h->t_diag);
   for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
   for (auto& W : h->work) {

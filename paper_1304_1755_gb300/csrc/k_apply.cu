@@ -46,6 +46,7 @@ struct ApplyArgs {
   const float* c32;
   const df2* cdf;
   const df2* wdf;      // optional table of weights c_k(e) gamma_n as double-float, slot-major
+  const double* w64;   // optional table of the same weights in FP64
   const int* ws;       // weight slot of each term
   const int* row_ptr;
   const int* tj;
@@ -114,6 +115,7 @@ template <> struct Load<DFS> {
 
 struct ArF32 {
   static constexpr bool kUsesTable = false;
+  static __host__ __device__ __forceinline__ const void* table(const ApplyArgs&) { return nullptr; }
   static constexpr int kUnroll = 4;        // couplings in flight per step (latency-bound stage updates)
   typedef float T;
   typedef float Acc;
@@ -138,15 +140,18 @@ struct ArF32 {
 };
 
 struct ArF64 {
-  static constexpr bool kUsesTable = false;
+  // with the weight table, the element is the FP64 product c_k(e) gamma of the term's slot (the
+  // same value the product below forms)
+  static constexpr bool kUsesTable = true;
   static constexpr int kUnroll = 2;
   typedef double T;
   typedef double Acc;
   typedef double G;
   typedef double CE;
+  static __host__ __device__ __forceinline__ const void* table(const ApplyArgs& a) { return a.w64; }
   static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.g64[t]; }
-  template <bool WT> static __device__ __forceinline__ const CE* cbase(const ApplyArgs& a) { return a.c64; }
-  template <bool WT> static __device__ __forceinline__ T weight(CE c, G g) { return c * g; }
+  template <bool WT> static __device__ __forceinline__ const CE* cbase(const ApplyArgs& a) { return WT ? a.w64 : a.c64; }
+  template <bool WT> static __device__ __forceinline__ T weight(CE c, G g) { return WT ? c : c * g; }
   static __device__ __forceinline__ Acc zero() { return 0.0; }
   static __device__ __forceinline__ T wzero() { return 0.0; }
   static __device__ __forceinline__ void fma(Acc& s, T w, float z) { s = ::fma(w, (double)z, s); }
@@ -168,6 +173,7 @@ struct ArDF {
   // with the weight table, k is the term's weight slot (precomputed c_k(e) gamma products)
   static constexpr bool kUsesTable = true;
   static constexpr int kUnroll = 2;
+  static __host__ __device__ __forceinline__ const void* table(const ApplyArgs& a) { return a.wdf; }
   typedef df2 G;
   typedef df2 CE;
   static __device__ __forceinline__ G gval(const ApplyArgs& a, int t) { return a.gdf[t]; }
@@ -417,7 +423,7 @@ int launch_t(sg_ctx* h, ApplyArgs& a) {
     if (gy <= 65535) break;
     a.strip *= 2;
   }
-  if (AR::kUsesTable && a.wdf)
+  if (AR::kUsesTable && AR::table(a))
     k_apply<AR, true, TXS, TYS, TRS><<<dim3((unsigned)a.nrows, (unsigned)gy), NT, 0, h->stream>>>(a);
   else
     k_apply<AR, false, TXS, TYS, TRS><<<dim3((unsigned)a.nrows, (unsigned)gy), NT, 0, h->stream>>>(a);
@@ -477,7 +483,7 @@ int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int
   ApplyArgs a{};
   a.X = X, a.xlo = xlo, a.Y = Y, a.ylo = ylo, a.R = R, a.rlo = rlo;
   a.c64 = h->coef64, a.c32 = h->coef32, a.cdf = (const df2*)h->coefdf;
-  a.wdf = (const df2*)h->wdf, a.ws = T.ws;
+  a.wdf = (const df2*)h->wdf, a.w64 = h->w64, a.ws = T.ws;
   a.row_ptr = T.row_ptr, a.tj = T.j, a.tk = T.k, a.g64 = T.g, a.g32 = T.gf, a.gdf = (const df2*)T.gdf;
   a.row0 = row0, a.nrows = nrows, a.ybase = ybase, a.rbase = rbase, a.n = h->n, a.m = h->m;
   a.Nx = h->Nx, a.Nc = h->Nc;

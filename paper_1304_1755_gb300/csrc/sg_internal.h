@@ -86,6 +86,7 @@ struct sg_ctx {
   float* coef32 = nullptr;
   float* coefdf = nullptr;              // (M+1) * Nc double-float pairs (hi, lo)
   float* wdf = nullptr;                 // (1 + M p) * Nc double-float weights c_k(e) gamma(n) (or null)
+  double* w64 = nullptr;                // the same weights in FP64 (or null)
   TermTable t_all, t_lower, t_upper, t_off, t_diag;   // all / lower / upper / off-diagonal / mean term
   double* pvec = nullptr;               // P doubles of device scratch (objective)
   // multigrid hierarchy
