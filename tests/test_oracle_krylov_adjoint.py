@@ -91,3 +91,89 @@ def test_block_gauss_seidel_and_bs_pcg_match_direct():
     U, its2, rr = krylov.pcg(Av, lambda r: precond.block_sym_inv(s, solver, r), F, tol=1e-12)
     assert rr <= 1e-12 and np.linalg.norm(U - Ud) / np.linalg.norm(Ud) < 1e-9
     assert its2 < its
+
+
+def _small(sigma=0.3):
+    """A small SG system (n = 9, M = 2, p = 2: 294 unknowns) with dense A and the two block
+    preconditioners as dense matrices (exact K_0 solves), for the Krylov optimality pins."""
+    n, M, p = 9, 2, 2
+    s = sg.build(n, M, p, basis.LEGENDRE, kl.kl_coefficients(n, M, sigma))
+    A = sg.assemble(s).toarray()
+    solver = precond.DiagSolver(s.K[0])                   # sparse LU of K_0
+    N = A.shape[0]
+    BTinv = np.column_stack([precond.block_tri_inv(s, solver, e) for e in np.eye(N)])
+    BDinv = np.column_stack([precond.block_diag_inv(s, solver, e) for e in np.eye(N)])
+    b = np.random.default_rng(11).standard_normal(N)
+    return A, BTinv, BDinv, b
+
+
+def _krylov_basis(Op, v, k):
+    """Orthonormal basis of span{v, Op v, ..., Op^(k-1) v} (Gram-Schmidt twice per vector)."""
+    Q = np.zeros((len(v), k))
+    w = v.copy()
+    for j in range(k):
+        for _ in range(2):
+            w = w - Q[:, :j] @ (Q[:, :j].T @ w)
+        Q[:, j] = w / np.linalg.norm(w)
+        w = Op @ Q[:, j]
+    return Q
+
+
+def test_gmres_iterate_minimises_the_residual_over_the_krylov_space():
+    """Right-preconditioned GMRES after k steps (no restart) returns the x in
+    x0 + M K_k(A M, r0) of least residual norm: brute-force least squares on that space."""
+    A, BTinv, _, b = _small()
+    AM = A @ BTinv
+    for k in (1, 2, 3, 5):
+        x, its, _ = krylov.gmres(lambda v: A @ v, lambda r: BTinv @ r, b, tol=1e-300, restart=30, maxit=k)
+        assert its == k
+        Q = _krylov_basis(AM, b, k)
+        y = np.linalg.lstsq(AM @ Q, b, rcond=None)[0]
+        best = np.linalg.norm(b - AM @ (Q @ y))
+        assert abs(np.linalg.norm(b - A @ x) - best) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_flexible_gmres_with_a_fixed_preconditioner_is_gmres():
+    """With the same linear preconditioner at every step, flexible GMRES builds the same iterate."""
+    A, BTinv, _, b = _small()
+    for k in (2, 4, 7):
+        x1 = krylov.gmres(lambda v: A @ v, lambda r: BTinv @ r, b, tol=1e-300, restart=30, maxit=k)[0]
+        x2 = krylov.gmres(lambda v: A @ v, lambda r: BTinv @ r, b, tol=1e-300, restart=30, maxit=k, flexible=True)[0]
+        assert np.linalg.norm(x1 - x2) <= 1e-11 * np.linalg.norm(x1)
+
+
+def test_pcg_iterate_minimises_the_energy_error_over_the_krylov_space():
+    """PCG with the SPD block-diagonal preconditioner after k steps returns the x in
+    K_k(M A, M b) of least A-norm error (x0 = 0): brute force by the projected normal equations."""
+    A, _, BDinv, b = _small()
+    xs = np.linalg.solve(A, b)
+    MA = BDinv @ A
+    for k in (1, 2, 4, 6):
+        x = krylov.pcg(lambda v: A @ v, lambda r: BDinv @ r, b, tol=1e-300, maxit=k)[0]
+        Q = _krylov_basis(MA, BDinv @ b, k)
+        y = np.linalg.solve(Q.T @ A @ Q, Q.T @ A @ xs)
+        xb = Q @ y
+        en = lambda z: np.sqrt((xs - z) @ A @ (xs - z))
+        assert abs(en(x) - en(xb)) <= 1e-9 * en(np.zeros_like(b))
+
+
+def test_gpcg1_with_a_symmetric_preconditioner_is_pcg():
+    """GPCG[1] orthogonalises each new direction against the previous one only; with a symmetric
+    positive definite preconditioner the conjugacy to all older directions holds by itself, so
+    its iterates are those of PCG."""
+    A, _, BDinv, b = _small()
+    for k in (1, 3, 6, 9):
+        x1 = krylov.gpcg1(lambda v: A @ v, lambda r: BDinv @ r, b, tol=1e-300, maxit=k)[0]
+        x2 = krylov.pcg(lambda v: A @ v, lambda r: BDinv @ r, b, tol=1e-300, maxit=k)[0]
+        assert np.linalg.norm(x1 - x2) <= 1e-9 * np.linalg.norm(x2)
+
+
+def test_block_gauss_seidel_error_is_the_matrix_power():
+    """The stationary iteration x <- x + B_T^-1 (b - A x) leaves the error (I - B_T^-1 A)^k e_0."""
+    A, BTinv, _, b = _small()
+    xs = np.linalg.solve(A, b)
+    E = np.eye(A.shape[0]) - BTinv @ A
+    for k in (1, 2, 5):
+        x = krylov.block_gauss_seidel(lambda v: A @ v, lambda r: BTinv @ r, b, tol=1e-300, maxit=k)[0]
+        e = np.linalg.matrix_power(E, k) @ (0 - xs)
+        assert np.linalg.norm((x - xs) - e) <= 1e-10 * np.linalg.norm(xs)
