@@ -18,9 +18,12 @@ GPCG[1].
 * ``pcg``: standard preconditioned conjugate gradients.
 
 Each returns (x, iterations, true relative residual).  Iterations count
-preconditioner applications.  Iteration counts are not pinned (the paper's
-counts are for another discretisation and smoother); the solutions are pinned
-against the direct solve.
+preconditioner applications.  Pins: the solutions against the direct solve;
+the k-step iterates against their defining minimisation (GMRES: least
+residual over x0 + M K_k; PCG: least energy error over K_k) by brute force on
+a small system, GPCG[1] with an SPD preconditioner against PCG, FGMRES with a
+fixed preconditioner against GMRES.  The paper's own iteration counts are for
+another discretisation and smoother, so they are not a pin.
 """
 import numpy as np
 
