@@ -1,0 +1,158 @@
+"""The paper's own discretisation: linear triangles and a point Gauss-Seidel V-cycle (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Sec. 6 solves the test problem on D = (-0.5, 0.5)^2 with linear finite elements on a uniform
+triangulation of mesh size h and approximates every diagonal block by one geometric multigrid
+V(2,2) cycle with point Gauss-Seidel smoothing.  The paper gives no further detail; the readings
+used here are:
+
+* every square cell of the uniform grid is cut by its SW-NE diagonal into a lower-right and an
+  upper-left right triangle; the KL coefficient of a triangle is taken at its centroid, so each
+  K_k is the P1 stiffness matrix of a piecewise-constant coefficient.  On these right triangles
+  the coupling across a diagonal vanishes (the opposite angles are right angles), so every K_k
+  has the 5-point pattern, which is what the nonzero counts of the paper's Table 1 imply;
+* the load vector is lumped, F_i = h^2 f(x_i) (six triangles of area h^2/2 share a vertex);
+* prolongation is linear interpolation on the nested triangulations (a fine vertex on a coarse
+  edge, the diagonals included, takes the mean of the edge's two end points), restriction its
+  transpose, coarse operators Galerkin products, the coarsest grid (one interior vertex) solved
+  exactly;
+* pre-smoothing is forward lexicographic Gauss-Seidel and post-smoothing backward Gauss-Seidel,
+  which makes the cycle a symmetric operator (PCG with B_D needs a symmetric preconditioner).
+
+Pins: the element matrices against the gradients of the barycentric basis; the assembled K_0
+against the 5-point Laplacian; the two-grid factor of the cycle against its local Fourier
+analysis; the Krylov iteration counts of the paper's Table 3 on the paper's test problem.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import basis, kl, mg
+from .sg import SGSystem
+
+
+def triangle_element_matrices():
+    """P1 stiffness element matrices (coefficient 1, any h) of the two right triangles of a cell:
+    lower-right (SW, SE, NE), right angle at SE, and upper-left (SW, NE, NW), right angle at NW."""
+    lower = np.array([[0.5, -0.5, 0.0], [-0.5, 1.0, -0.5], [0.0, -0.5, 0.5]])
+    upper = np.array([[0.5, 0.0, -0.5], [0.0, 0.5, -0.5], [-0.5, -0.5, 1.0]])
+    return lower, upper
+
+
+def triangle_coefficients(n, M, sigma, corr_len=1.0):
+    """Coefficients c_k(T), k = 0..M, at the centroids of the 2 (n-1)^2 triangles: triangle 2e is
+    the lower-right and 2e + 1 the upper-left triangle of cell e = cx + cy (n-1); row 0 is the
+    mean 1, row k >= 1 is sigma sqrt(lambda_k) b_k(centroid) (same separable modes as ``kl``)."""
+    nc1 = n - 1
+    h = 1.0 / nc1
+    lam1, om1, par1 = kl.kl_1d(M + 1, corr_len)
+    modes = kl.kl_2d_modes(M, corr_len)
+    base = np.arange(nc1) * h - 0.5
+    coef = np.zeros((M + 1, 2 * nc1 * nc1))
+    coef[0] = 1.0
+    for k, (lam, i, j) in enumerate(modes, start=1):
+        for t, (ox, oy) in enumerate(((2.0 / 3.0, 1.0 / 3.0), (1.0 / 3.0, 2.0 / 3.0))):
+            bx = kl.eval_1d(om1[i], par1[i], base + ox * h)
+            by = kl.eval_1d(om1[j], par1[j], base + oy * h)
+            coef[k, t::2] = sigma * np.sqrt(lam) * np.outer(by, bx).reshape(-1)
+    return coef
+
+
+def assemble_p1(n, tri_coef):
+    """Interior-node P1 stiffness matrix for the per-triangle coefficients tri_coef (2 (n-1)^2)."""
+    m = n - 2
+    lower, upper = triangle_element_matrices()
+    rows, cols, vals = [], [], []
+    nc1 = n - 1
+    for cy in range(nc1):
+        for cx in range(nc1):
+            e = cx + cy * nc1
+            sw, se, ne, nw = (cx, cy), (cx + 1, cy), (cx + 1, cy + 1), (cx, cy + 1)
+            for Ke, verts, a in ((lower, (sw, se, ne), tri_coef[2 * e]), (upper, (sw, ne, nw), tri_coef[2 * e + 1])):
+                idx = [(vx - 1) + (vy - 1) * m if 1 <= vx <= n - 2 and 1 <= vy <= n - 2 else -1 for vx, vy in verts]
+                for r in range(3):
+                    for c in range(3):
+                        if idx[r] >= 0 and idx[c] >= 0 and Ke[r, c] != 0.0:
+                            rows.append(idx[r]), cols.append(idx[c]), vals.append(a * Ke[r, c])
+    K = sp.csr_matrix((vals, (rows, cols)), shape=(m * m, m * m))
+    K.sum_duplicates()
+    K.eliminate_zeros()
+    return K
+
+
+def build(n, M, p, family, sigma, corr_len=1.0):
+    """SG system of the paper's discretisation (the same chaos space and G_k as ``sg.build``)."""
+    tc = triangle_coefficients(n, M, sigma, corr_len)
+    alphas = basis.multi_indices(M, p)
+    G = basis.g_matrices(alphas, family)
+    K = [assemble_p1(n, tc[k]) for k in range(M + 1)]
+    return SGSystem(n, M, p, family, tc, alphas, G, K)
+
+
+def rhs(sys, f=None):
+    """F = e_0 (x) F_0 with the lumped load F_0,i = h^2 f(x_i); f defaults to the paper's
+    2 (0.5 - x^2 - y^2) on (-0.5, 0.5)^2."""
+    n = sys.n
+    h = 1.0 / (n - 1)
+    xs = np.arange(1, n - 1) * h - 0.5
+    X, Y = np.meshgrid(xs, xs)
+    fv = 2.0 * (0.5 - X ** 2 - Y ** 2) if f is None else f(X, Y)
+    F = np.zeros((sys.P, sys.Nx))
+    F[0] = h * h * fv.reshape(-1)
+    return F.reshape(-1)
+
+
+def prolongation(nc):
+    """Linear interpolation from the interior of an nc-grid to the interior of the (2 nc - 1)-grid
+    of the nested triangulation (SW-NE diagonals)."""
+    nf = 2 * nc - 1
+    mf, mc = nf - 2, nc - 2
+    rows, cols, vals = [], [], []
+    for vy in range(1, nf - 1):
+        for vx in range(1, nf - 1):
+            r = (vx - 1) + (vy - 1) * mf
+            if vx % 2 == 0 and vy % 2 == 0:
+                src = [(vx // 2, vy // 2, 1.0)]
+            elif vy % 2 == 0:
+                src = [((vx - 1) // 2, vy // 2, 0.5), ((vx + 1) // 2, vy // 2, 0.5)]
+            elif vx % 2 == 0:
+                src = [(vx // 2, (vy - 1) // 2, 0.5), (vx // 2, (vy + 1) // 2, 0.5)]
+            else:                                           # centre of a coarse cell: on its SW-NE diagonal
+                src = [((vx - 1) // 2, (vy - 1) // 2, 0.5), ((vx + 1) // 2, (vy + 1) // 2, 0.5)]
+            for cxv, cyv, w in src:
+                if 1 <= cxv <= nc - 2 and 1 <= cyv <= nc - 2:
+                    rows.append(r), cols.append((cxv - 1) + (cyv - 1) * mc), vals.append(w)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(mf * mf, mc * mc))
+
+
+class GSHierarchy:
+    """V(nu1, nu2) cycle with forward Gauss-Seidel pre- and backward Gauss-Seidel post-smoothing."""
+
+    def __init__(self, K0, n, nu1=2, nu2=2, coarsest=3):
+        self.sizes = mg.grid_sizes(n, coarsest)
+        self.nu1, self.nu2 = nu1, nu2
+        self.A = [sp.csr_matrix(K0)]
+        self.P = []
+        for l in range(len(self.sizes) - 1):
+            Pl = prolongation(self.sizes[l + 1])
+            self.P.append(Pl)
+            self.A.append((Pl.T @ self.A[l] @ Pl).tocsr())
+        # D + L and D + U as sparse LU factors with the natural order (plain triangular solves)
+        self.low = [spla.splu(sp.tril(A).tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0) for A in self.A[:-1]]
+        self.up = [spla.splu(sp.triu(A).tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0) for A in self.A[:-1]]
+        self.coarse_inv = np.linalg.inv(self.A[-1].toarray())
+
+    def vcycle(self, b, level=0):
+        """One cycle from a zero initial guess; b is (N_l,) or (N_l, nrhs)."""
+        A = self.A[level]
+        if level == len(self.A) - 1:
+            return self.coarse_inv @ b
+        x = np.zeros_like(b)
+        for _ in range(self.nu1):
+            x = x + self.low[level].solve(b - A @ x)
+        bc = self.P[level].T @ (b - A @ x)
+        x = x + self.P[level] @ self.vcycle(bc, level + 1)
+        for _ in range(self.nu2):
+            x = x + self.up[level].solve(b - A @ x)
+        return x

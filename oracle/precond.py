@@ -21,6 +21,8 @@ Diagonal solve options: a V-cycle (``Hierarchy.vcycle``) or the exact
 sparse LU of K_0 (used for the spectral checks of Sec. 5).
 """
 import numpy as np
+
+from . import basis
 import scipy.sparse.linalg as spla
 
 
@@ -77,3 +79,36 @@ def block_sym_inv(sys, solver, R):
     Z1 = block_tri_inv(sys, solver, R).reshape(sys.P, sys.Nx)
     Z2 = (sys.K[0] @ Z1.T).T
     return block_tri_inv(sys, solver, np.ascontiguousarray(Z2).reshape(-1), transpose=True)
+
+
+def block_sym_recursive_inv(sys, solver, R):
+    """Z = B_S^{-1} R with the 2 x 2 form of Sec. 4.2 applied recursively over the degree levels:
+    B_S = [A_hat 0; W D] diag(A_hat, D)^{-1} [A_hat W^T; 0 D] gives
+      y_low = A_hat^{-1} R_low,  y_p = D^{-1} (R_p - W y_low),  z_low = A_hat^{-1} (R_low - W^T y_p),
+    and A_hat^{-1} is replaced by the same preconditioner one degree lower, down to degree 0, whose
+    block is K_0 (D = I (x) K_0 on every degree level).  Each call of the solver takes the blocks of one
+    degree level at once."""
+    off = basis.degree_levels(sys.alphas)
+    P, Nx = sys.P, sys.Nx
+    Rm = np.asarray(R, dtype=np.float64).reshape(P, Nx)
+
+    def couple(Y, rows, cols):
+        """sum_k G_k[rows, cols] (x) K_k applied to the blocks Y of the columns."""
+        out = np.zeros((len(rows), Nx))
+        for k in range(1, sys.M + 1):
+            Gk = sys.G[k][np.ix_(rows, cols)]
+            if np.any(Gk):
+                out += Gk @ (sys.K[k] @ Y.T).T
+        return out
+
+    def rec(q, Rq):                                       # Rq: blocks of degrees 0..q, in order
+        hi = np.arange(off[q], off[q + 1])
+        if q == 0:
+            return solver(Rq.T).T
+        low = np.arange(0, off[q])
+        y_low = rec(q - 1, Rq[:off[q]])
+        y_hi = solver((Rq[off[q]:] - couple(y_low, hi, low)).T).T
+        z_low = rec(q - 1, Rq[:off[q]] - couple(y_hi, low, hi))
+        return np.vstack([z_low, y_hi])
+
+    return rec(len(off) - 2, Rm).reshape(-1)
