@@ -26,9 +26,9 @@ Gauss-Seidel multigrid on the coupled system A_hat itself (``CoupledGSHierarchy`
 ``block_tri_2x2_inv``), and the degree-p blocks by K_0 cycles.
 
 Pins: the element matrices against the gradients of the barycentric basis; the assembled K_0
-against the 5-point Laplacian and the nonzero count of Table 1; the symmetry of the cycle (its
-contraction only in a sanity band: parity unpinned for the factor itself); the iteration counts the
-paper prints in Tables 2 and 3 for its test problem.
+against the 5-point Laplacian and the nonzero count of Table 1; the symmetry of the cycle and its
+two-grid factor against a local Fourier analysis of lexicographic Gauss-Seidel; the iteration
+counts the paper prints in Tables 2 and 3 for its test problem.
 """
 import numpy as np
 import scipy.sparse as sp
