@@ -772,10 +772,11 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
     if ((o.method == SG_GMRES || o.method == SG_FGMRES) && is_pinned_host(U)) h->spec_dst = U;
     if (!h->dstage && cudaMalloc(&h->dstage, sizeof(double) * N * 2) != cudaSuccess)
       return sg_fail(h, SG_E_ALLOC, "sg_solve: staging allocation");
-    SG_CUDA(h, cudaMemcpyAsync(h->dstage, F, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    // cudaMemcpyDefault: one of F and U may be a device pointer (the runtime infers each direction)
+    SG_CUDA(h, cudaMemcpyAsync(h->dstage, F, sizeof(double) * N, cudaMemcpyDefault, h->stream));
     dF = h->dstage;
     dU = h->dstage + N;
-    if (o.x0_given) SG_CUDA(h, cudaMemcpyAsync(dU, U, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    if (o.x0_given) SG_CUDA(h, cudaMemcpyAsync(dU, U, sizeof(double) * N, cudaMemcpyDefault, h->stream));
   }
   cudaEvent_t e0, e1;
   SG_CUDA(h, cudaEventCreate(&e0));
@@ -805,7 +806,7 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
     } else {
       int rc3 = spec_invalidate(h);
       if (rc3) return rc3;
-      SG_CUDA(h, cudaMemcpyAsync(U, dU, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+      SG_CUDA(h, cudaMemcpyAsync(U, dU, sizeof(double) * N, cudaMemcpyDefault, h->stream));
     }
   } else if (h->spec_pending) {
     SG_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_c, 0));   // no copy in flight past the call
