@@ -92,14 +92,18 @@ def _counts(n, M, p, sigma, methods):
 
 
 def test_table2_uniform_iterations_with_the_papers_discretisation():
-    """Table 2: at sigma = 0.1 the counts do not depend on h, p or m, and they are the paper's to
-    within one iteration (BD-PCG 13, BT-GPCG 9, BS-PCG 9, BT-GMRes 8)."""
+    """Table 2: at sigma = 0.1 the counts do not depend on h, p or m (h = 1/32 and 1/64, p = 2 and 3,
+    m = 4 and 6), and they are the paper's to within one iteration (BD-PCG 13, BT-GPCG 9, BS-PCG 9,
+    BT-GMRes 8), also at h = 1/128."""
     names = ["BD-PCG", "BT-GPCG", "BS-PCG", "BT-GMRes"]
     runs = [_counts(n, M, p, 0.1, names) for n, M, p in ((33, 4, 2), (33, 6, 2), (33, 4, 3), (65, 4, 2))]
     for r in runs[1:]:
         assert r == runs[0]
     for name in names:
         assert abs(runs[0][name] - GOLDEN["table2"][name]) <= 1, (name, runs[0][name])
+    fine = _counts(129, 4, 2, 0.1, names)                 # h = 1/128
+    for name in names:
+        assert abs(fine[name] - GOLDEN["table2"][name]) <= 1, (name, fine[name])
 
 
 @pytest.mark.parametrize("sigma,methods", [
