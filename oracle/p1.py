@@ -216,3 +216,45 @@ def block_tri_2x2_inv(sys, ahat_cycle, solver, R):
             T -= Gk @ (sys.K[k] @ Zlow.T).T
     Zp = solver(T.T).T
     return np.vstack([Zlow, Zp]).reshape(-1)
+
+
+class MulticolourCoupledGSHierarchy(CoupledGSHierarchy):
+    """The coupled cycle with the parallel (multicolour) Gauss-Seidel order: an unknown (PC row i,
+    node (x, y)) has colour 2 (deg(i) mod 2) + ((x + y) mod 2).  The K_k are 5-point, so a coupling
+    between two nodes joins opposite node parities, and G_k (k >= 1) couples only degrees one apart
+    (G_0 = I), so no two unknowns of one colour are coupled and a colour is updated at once.
+    Pre-smoothing visits the colours 0, 1, 2, 3 and post-smoothing 3, 2, 1, 0 (a symmetric cycle)."""
+
+    def __init__(self, sys, rows, nu1=2, nu2=2, coarsest=3):
+        super().__init__(sys, rows, nu1, nu2, coarsest)
+        rows = np.asarray(rows)
+        degs = np.array([sum(sys.alphas[i]) for i in rows])
+        sizes = mg.grid_sizes(sys.n, coarsest)
+        self.colours, self.dinv = [], []
+        for l, nl in enumerate(sizes[:-1]):
+            m = nl - 2
+            vx, vy = np.meshgrid(np.arange(m), np.arange(m))
+            parity = ((vx + vy) % 2).reshape(-1)
+            colour = np.repeat(degs % 2, m * m) * 2 + np.tile(parity, len(rows))
+            self.colours.append([np.nonzero(colour == c)[0] for c in range(4)])
+            self.dinv.append(1.0 / self.A[l].diagonal())
+
+    def _sweep(self, level, x, b, order):
+        A = self.A[level]
+        for c in order:
+            idx = self.colours[level][c]
+            d = self.dinv[level][idx] if b.ndim == 1 else self.dinv[level][idx][:, None]
+            x[idx] += d * (b[idx] - A[idx] @ x)
+        return x
+
+    def vcycle(self, b, level=0):
+        A = self.A[level]
+        if level == len(self.A) - 1:
+            return self.coarse_inv @ b
+        x = np.zeros_like(b)
+        for _ in range(self.nu1):
+            x = self._sweep(level, x, b, (0, 1, 2, 3))
+        x = x + self.P[level] @ self.vcycle(self.P[level].T @ (b - A @ x), level + 1)
+        for _ in range(self.nu2):
+            x = self._sweep(level, x, b, (3, 2, 1, 0))
+        return x

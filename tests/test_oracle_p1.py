@@ -209,3 +209,22 @@ def test_gauss_seidel_two_grid_factor_matches_local_fourier_analysis(nu1, nu2):
         e = e_new / np.linalg.norm(e_new)
     rl = _lfa_gs_two_grid(nu1, nu2)
     assert 0.97 * rl <= r <= 1.005 * rl, (r, rl)
+
+
+def test_four_colour_order_has_no_coupling_inside_a_colour():
+    """The colours of MulticolourCoupledGSHierarchy are independent sets of the coupled lower-degree
+    matrix on every level (each colour block of A is diagonal), so a colour sweep is an exact Gauss-Seidel
+    step; the cycle (colours 0-3 before, 3-0 after) is a symmetric operator."""
+    n = 9
+    s = p1.build(n, 2, 3, basis.LEGENDRE, 0.3)
+    off = basis.degree_levels(s.alphas)
+    cyc = p1.MulticolourCoupledGSHierarchy(s, np.arange(off[-2]))
+    for l, cols in enumerate(cyc.colours):
+        A = cyc.A[l].tocsr()
+        assert sum(len(c) for c in cols) == A.shape[0]
+        for c in cols:
+            sub = A[c][:, c].tocoo()
+            assert np.all(sub.row[np.abs(sub.data) > 0] == sub.col[np.abs(sub.data) > 0])
+    N = cyc.A[0].shape[0]
+    B = cyc.vcycle(np.eye(N))
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
