@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
 its Python binding) may import, call, link or execute anything in this
 package; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
-leg of ``bench.py`` may.  The oracle shares no code with the CUDA path: the
+and reference legs of ``bench.py`` may.  The oracle shares no code with the CUDA path: the
 only module both sides use is the seeded input generator
 ``paper_1304_1755_gb300.inputs``, which holds none of the method's arithmetic.
 
@@ -20,9 +20,14 @@ Modules
   sg       global Galerkin matrix A = sum_k G_k (x) K_k (Eq. tensor-product),
            direct solve and unpreconditioned GMRES
   mg       geometric multigrid V-cycle on the mean operator (Sec. 4.1, 6)
-  precond  block-diagonal B_D and block-triangular B_T (Sec. 4.1, 4.2)
-  krylov   right-preconditioned (F)GMRES, GPCG[1], PCG (Sec. 4.2, 6)
+  precond  block-diagonal B_D, block-triangular B_T and the symmetric B_S (flat
+           and recursive 2 x 2 forms) (Sec. 4.1, 4.2)
+  krylov   right-preconditioned (F)GMRES, GPCG[1], PCG, block Gauss-Seidel
+           (Sec. 4.2, 6)
   adjoint  objective E[int u] + Var[int u]/2 and its adjoint gradient
+  p1       the paper's own discretisation of its test problem: P1 triangles,
+           point Gauss-Seidel V(2,2), and the coupled-cycle reading of B_T (Sec. 6)
+  reproduce_tables  prints the counts of Tables 2 and 3 under each reading
 
 Parity pins: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, an independent quadrature, brute force, an invariant or a
