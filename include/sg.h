@@ -207,6 +207,8 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
 /* Solve nsys independent systems, each with its own handle (any mix of grids, M and p;
  * the batched form of the method's solve, Sec. 4.2 / 6, for many problems at once).
  * hs[s], F[s], U[s] as in sg_solve (device pointers); the same opts for every system.
+ * The handles must be distinct (a handle's workspace serves one solve at a time); a repeated
+ * handle is rejected with SG_E_ARG before any work starts.
  * nstreams (1..64) worker threads each drive one CUDA stream created for the call and
  * take the systems largest first; each handle's own stream is restored afterwards.
  * infos (may be NULL) receives one sg_solve_info per system, with status set to that

@@ -23,6 +23,12 @@ extern "C" int sg_solve_batch(sg_handle* hs, const double* const* F, double* con
   for (int s = 0; s < nsys; ++s)
     if (!hs[s] || !F[s] || !U[s]) return SG_E_ARG;
   if (nsys == 0) return SG_OK;
+  {
+    // a handle's workspace serves one solve at a time: every system needs its own handle
+    std::vector<sg_handle> seen(hs, hs + nsys);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return SG_E_ARG;
+  }
   std::vector<int> order(nsys);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {

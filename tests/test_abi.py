@@ -51,6 +51,18 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.sg_setup(ctypes.byref(prob), None, ctypes.byref(h)) == -1
 
 
+def test_batch_rejects_a_repeated_handle_without_device(lib):
+    """A handle listed twice is rejected before anything is read through it (the addresses below are
+    never dereferenced)."""
+    from paper_1304_1755_gb300 import sg
+    import ctypes
+    fake = ctypes.c_void_p(0x1000)
+    hs = (sg.VP * 2)(fake, fake)
+    vecs = (sg.VP * 2)(ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000))
+    o = sg.SolveOpts(sg.FGMRES, sg.PC_BLOCKTRI, 30, 100, 1e-8, sg.F32, 0, 0, 0, 0)
+    assert lib.sg_solve_batch(hs, vecs, vecs, 2, ctypes.byref(o), None, 2) == -1
+
+
 @pytest.mark.parametrize("n,M,sigma", [(9, 2, 0.3), (33, 4, 0.5), (17, 6, 0.2)])
 def test_library_kl_helper_matches_oracle(lib, n, M, sigma):
     from oracle import kl
