@@ -51,6 +51,38 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.sg_setup(ctypes.byref(prob), None, ctypes.byref(h)) == -1
 
 
+def test_every_entry_point_rejects_a_null_handle_without_device(lib):
+    """Every call that takes a handle returns SG_E_ARG for a null one (and sg_destroy ignores it),
+    before touching the device."""
+    from paper_1304_1755_gb300 import sg
+    import ctypes
+    D, I = ctypes.c_double(), ctypes.c_int()
+    o = sg.SolveOpts(sg.FGMRES, sg.PC_BLOCKTRI, 30, 100, 1e-8, sg.F32, 0, 0, 0, 0)
+    info = sg.SolveInfo()
+    ms, ln = (ctypes.c_double * 4)(), (ctypes.c_long * 4)()
+    calls = [
+        lambda: lib.sg_set_stream(None, None),
+        lambda: lib.sg_sizes(None, ctypes.byref(I), ctypes.byref(I), ctypes.byref(I)),
+        lambda: lib.sg_basis(None, None),
+        lambda: lib.sg_apply(None, None, None, 0),
+        lambda: lib.sg_residual(None, None, None, None),
+        lambda: lib.sg_precond_blocktri(None, None, None, 0, 0),
+        lambda: lib.sg_precond_blockdiag(None, None, None, 0),
+        lambda: lib.sg_precond_blocksym(None, None, None, 0),
+        lambda: lib.sg_vcycle(None, None, None, 1, 0),
+        lambda: lib.sg_vcycle_static(None, None, None, 1, 0),
+        lambda: lib.sg_solve(None, None, None, ctypes.byref(o), ctypes.byref(info)),
+        lambda: lib.sg_autotune(None, 0),
+        lambda: lib.sg_objective(None, None, ctypes.byref(D), None),
+        lambda: lib.sg_adjoint_gradients(None, None, None, 0.1, None, ctypes.byref(D)),
+        lambda: lib.sg_timing_enable(None, 1),
+        lambda: lib.sg_timing_read(None, ms, ln),
+    ]
+    for call in calls:
+        assert call() == -1
+    lib.sg_destroy(None)
+
+
 def test_batch_rejects_a_repeated_handle_without_device(lib):
     """A handle listed twice is rejected before anything is read through it (the addresses below are
     never dereferenced)."""
