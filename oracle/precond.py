@@ -112,3 +112,29 @@ def block_sym_recursive_inv(sys, solver, R):
         return np.vstack([z_low, y_hi])
 
     return rec(len(off) - 2, Rm).reshape(-1)
+
+
+def block_tri_exact_inv(sys, solver, R, inner_tol=1e-13, inner_restart=40):
+    """Z = B_T^{-1} R for the 2 x 2 split of Theorem 1 with the lower-degree block A_hat solved to
+    ``inner_tol`` (GMRES on A_hat, right-preconditioned by the flat B_T of A_hat) and the degree-p
+    blocks by ``solver``:  Z_low = A_hat^{-1} R_low,  Z_p = D^{-1} (R_p - W Z_low).  An analysis tool
+    (Sec. 4.2, Theorem 1): with an exact ``solver`` its preconditioned spectrum is the theorem's."""
+    from . import krylov
+    from .sg import SGSystem, apply as sg_apply
+    off = basis.degree_levels(sys.alphas)
+    P, Nx = sys.P, sys.Nx
+    nlow = off[-2]
+    Rm = np.asarray(R, dtype=np.float64).reshape(P, Nx)
+    low = SGSystem(sys.n, sys.M, sys.p - 1, sys.family, sys.coef, list(sys.alphas[:nlow]),
+                   [G[:nlow, :nlow] for G in sys.G], sys.K)
+    Zlow, _, rr = krylov.gmres(lambda v: sg_apply(low, v), lambda r: block_tri_inv(low, solver, r),
+                               Rm[:nlow].reshape(-1), tol=inner_tol, restart=inner_restart, maxit=2000)
+    Zlow = Zlow.reshape(nlow, Nx)
+    T = Rm[nlow:].copy()
+    hi, lo = np.arange(nlow, P), np.arange(nlow)
+    for k in range(1, sys.M + 1):
+        Gk = sys.G[k][np.ix_(hi, lo)]
+        if np.any(Gk):
+            T -= Gk @ (sys.K[k] @ Zlow.T).T
+    Zp = solver(T.T).T
+    return np.vstack([Zlow, Zp]).reshape(-1)

@@ -215,3 +215,15 @@ def test_block_sym_is_dense_bs_and_spd():
     R = np.random.default_rng(5).standard_normal(s.P * s.Nx)
     solver = precond.DiagSolver(s.K[0])
     assert np.allclose(precond.block_sym_inv(s, solver, R), np.linalg.solve(BS, R), atol=1e-12)
+
+
+def test_exact_lower_block_triangular_application_is_the_dense_two_by_two_inverse():
+    """block_tri_exact_inv (A_hat by inner GMRES to 1e-13, D by exact K_0 solves) applies the dense
+    [A_hat 0; W D]^-1 of Theorem 1 to a random vector."""
+    s = _system(n=9, M=2, p=3, sigma=0.4)
+    A, Ah, W, D = _split(s)
+    BT = np.block([[Ah, np.zeros_like(W.T)], [W, D]])
+    r = np.random.default_rng(9).standard_normal(A.shape[0])
+    z = precond.block_tri_exact_inv(s, precond.DiagSolver(s.K[0]), r)
+    zd = np.linalg.solve(BT, r)
+    assert np.linalg.norm(z - zd) <= 1e-9 * np.linalg.norm(zd)
