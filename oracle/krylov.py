@@ -16,6 +16,8 @@ GPCG[1].
   d = g - (<A g, d'> / <A d', d'>) d' is A-orthogonalised against the previous
   direction d'; alpha = <r, d> / <A d, d>; x += alpha d; r -= alpha A d.
 * ``pcg``: standard preconditioned conjugate gradients.
+* ``gmres_left``: restarted GMRES on M^{-1} A x = M^{-1} b, stopping on the preconditioned
+  residual (a reading of the paper's Table 3 runs, see the function).
 
 Each returns (x, iterations, true relative residual).  Iterations count
 preconditioner applications.  Pins: the solutions against the direct solve;
@@ -79,6 +81,58 @@ def gmres(apply_A, apply_M, b, x0=None, tol=1e-8, restart=30, maxit=1000, flexib
                 x = x + y[i] * Z[i]
         else:
             x = x + Minv(sum(y[i] * V[i] for i in range(k)))
+
+
+def gmres_left(apply_A, apply_M, b, x0=None, tol=1e-8, restart=30, maxit=1000):
+    """Restarted GMRES on the left-preconditioned system M^{-1} A x = M^{-1} b, stopping when the
+    preconditioned residual ||M^{-1}(b - A x)|| <= tol ||M^{-1} b|| (the criterion of a left-
+    preconditioned GMRES such as MATLAB's, which the paper's Table 3 runs were made with; the paper
+    states only "relative residual").  Classical Gram-Schmidt run twice per step, Givens rotations.
+    Returns (x, iterations, true relative residual ||b - A x|| / ||b||)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    pbnorm = np.linalg.norm(apply_M(b))
+    if bnorm == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    its = 0
+    while True:
+        r = apply_M(b - apply_A(x))
+        beta = np.linalg.norm(r)
+        if beta <= tol * pbnorm or its >= maxit:
+            return x, its, np.linalg.norm(b - apply_A(x)) / bnorm
+        V = [r / beta]
+        H = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        k = 0
+        for j in range(restart):
+            w = apply_M(apply_A(V[j]))
+            for _ in range(2):
+                for i in range(j + 1):
+                    c = np.dot(V[i], w)
+                    H[i, j] += c
+                    w = w - c * V[i]
+            hnext = np.linalg.norm(w)
+            H[j + 1, j] = hnext
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j] = d
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            if abs(g[j + 1]) <= tol * pbnorm or its >= maxit or hnext == 0.0:
+                break
+            V.append(w / hnext)
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + sum(y[i] * V[i] for i in range(k))
 
 
 def gpcg1(apply_A, apply_M, b, x0=None, tol=1e-8, maxit=1000):

@@ -44,6 +44,7 @@ def table3_counts(sigma, n=65, M=6, p=4):
         out["Block-GS " + tag] = krylov.block_gauss_seidel(Ax, bt, F, tol=1e-10, maxit=400)[1]
         out["BT-GPCG " + tag] = krylov.gpcg1(Ax, bt, F, tol=1e-10, maxit=400)[1]
         out["BT-GMRes " + tag] = krylov.gmres(Ax, bt, F, tol=1e-10, restart=10, maxit=400)[1]
+        out["BT-GMRes-left " + tag] = krylov.gmres_left(Ax, bt, F, tol=1e-10, restart=10, maxit=400)[1]
     out["BD-PCG"] = krylov.pcg(Ax, lambda r: precond.block_diag_inv(s, solver, r), F, tol=1e-10, maxit=400)[1]
     out["BS-PCG flat"] = krylov.pcg(Ax, lambda r: precond.block_sym_inv(s, solver, r), F, tol=1e-10, maxit=400)[1]
     out["BS-PCG recursive"] = krylov.pcg(Ax, lambda r: precond.block_sym_recursive_inv(s, solver, r), F, tol=1e-10,
@@ -82,7 +83,7 @@ def main():
         c = table3_counts(sigma)
         print(f"sigma = {sigma}", flush=True)
         for k, v in c.items():
-            method = k.split(" ")[0]
+            method = k.split(" ")[0].replace("-left", "")
             print(f"  {k:22s} {v:4d}   paper {t3[method][j][0]}", flush=True)
 
 

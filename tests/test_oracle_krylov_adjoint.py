@@ -177,3 +177,18 @@ def test_block_gauss_seidel_error_is_the_matrix_power():
         x = krylov.block_gauss_seidel(lambda v: A @ v, lambda r: BTinv @ r, b, tol=1e-300, maxit=k)[0]
         e = np.linalg.matrix_power(E, k) @ (0 - xs)
         assert np.linalg.norm((x - xs) - e) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_left_gmres_iterate_minimises_the_preconditioned_residual():
+    """Left-preconditioned GMRES after k steps (no restart) returns the x in K_k(M A, M b) of least
+    preconditioned residual ||M (b - A x)||: brute-force least squares on that space."""
+    A, BTinv, _, b = _small()
+    MA = BTinv @ A
+    Mb = BTinv @ b
+    for k in (1, 2, 4, 6):
+        x, its, _ = krylov.gmres_left(lambda v: A @ v, lambda r: BTinv @ r, b, tol=1e-300, restart=30, maxit=k)
+        assert its == k
+        Q = _krylov_basis(MA, Mb, k)
+        y = np.linalg.lstsq(MA @ Q, Mb, rcond=None)[0]
+        best = np.linalg.norm(Mb - MA @ (Q @ y))
+        assert abs(np.linalg.norm(Mb - MA @ x) - best) <= 1e-10 * np.linalg.norm(Mb)

@@ -147,12 +147,14 @@ def test_recursive_symmetric_preconditioner_is_the_dense_recursion():
     assert np.linalg.eigvalsh(0.5 * (Z + Z.T)).min() > 0
 
 
-@pytest.mark.parametrize("sigma", [0.1, 0.2])
+@pytest.mark.parametrize("sigma", [0.1, 0.2, 0.3])
 def test_table3_block_triangular_with_a_coupled_cycle_on_the_lower_degrees(sigma):
     """Reading of B_T that the paper's counts support: the 2 x 2 split with A_hat (all degrees < p,
     coupled) approximated by one point Gauss-Seidel V(2,2) of the coupled system and the degree-p
-    blocks by K_0 cycles.  GPCG[1] and block Gauss-Seidel then need the paper's counts to within one
-    (the flat block substitution needs 12 and 19 at sigma = 0.2 against the paper's 10 and 16)."""
+    blocks by K_0 cycles.  GPCG[1], and GMRes(10) run as a left-preconditioned GMRES that stops on the
+    preconditioned residual, then need the paper's counts to within one (the flat block substitution
+    with right-preconditioned GMRES needs 12 and 11 at sigma = 0.2 against the paper's 10 and 9); block
+    Gauss-Seidel too, for sigma <= 0.2 (26 against 24 at sigma = 0.3)."""
     n = 65
     s = p1.build(n, 6, 4, basis.LEGENDRE, sigma)
     F = p1.rhs(s)
@@ -164,9 +166,11 @@ def test_table3_block_triangular_with_a_coupled_cycle_on_the_lower_degrees(sigma
     t3 = GOLDEN["table3"]
     col = t3["sigma"].index(sigma)
     got = {"BT-GPCG": krylov.gpcg1(Ax, bt, F, tol=1e-10, maxit=400),
-           "Block-GS": krylov.block_gauss_seidel(Ax, bt, F, tol=1e-10, maxit=400)}
+           "BT-GMRes": krylov.gmres_left(Ax, bt, F, tol=1e-10, restart=10, maxit=400)}
+    if sigma <= 0.2:
+        got["Block-GS"] = krylov.block_gauss_seidel(Ax, bt, F, tol=1e-10, maxit=400)
     for name, (x, its, rr) in got.items():
-        assert rr <= 1e-10
+        assert rr <= (1e-10 if name != "BT-GMRes" else 1e-7)   # left GMRES stops on the preconditioned residual
         assert abs(its - t3[name][col][0]) <= 1, (name, its, t3[name][col][0])
 
 
