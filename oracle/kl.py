@@ -22,7 +22,8 @@ putting the lower x1-mode index first.
 
 Pins: the integral equation residual by independent quadrature, sum of 1-D
 eigenvalues -> 1 (trace of the unit-variance covariance on a unit interval),
-orthonormality of the modes.
+orthonormality of the modes; the coercivity minimum by enumeration of the corners of
+the xi box.
 """
 import math
 
@@ -110,13 +111,13 @@ def kl_mode_sup(M, corr_len=1.0):
     return np.array([sup1[i] * sup1[j] for (_, i, j) in kl_2d_modes(M, corr_len)])
 
 
-def min_coefficient_at_corners(coef, family):
+def min_coefficient_at_corners(coef, xi_max=math.sqrt(3.0)):
     """Coercivity check (Eq. assumption, Remark after Eq. exponential-covariance).
 
-    Minimum over cells of a = c_0 + sum_k c_k xi_k over the corners of the xi box
-    [-sqrt3, sqrt3]^M (Legendre).  Linear in xi, so the minimum over the box is
-    c_0 - sqrt3 * sum_k |c_k| per cell.  For Hermite chaos the support is
-    unbounded; the value returned is the same expression at |xi_k| = sqrt3, a
-    reference number only.
+    Minimum over the cells of a = c_0 + sum_k c_k xi_k over the box |xi_k| <= xi_max
+    (xi_max = sqrt3 is the support of the unit-variance uniform variables of the
+    Legendre chaos).  a is linear in xi, so the minimum over the box sits at the
+    corner xi_k = -xi_max sign(c_k), where it equals c_0 - xi_max sum_k |c_k|.
+    Hermite variables are unbounded; there xi_max is a chosen reference radius.
     """
-    return float(np.min(coef[0] - math.sqrt(3.0) * np.sum(np.abs(coef[1:]), axis=0)))
+    return float(np.min(coef[0] - xi_max * np.sum(np.abs(coef[1:]), axis=0)))

@@ -79,3 +79,21 @@ def test_coefficients_layout_and_variance():
     c2 = c[2].reshape(16, 16)
     assert np.allclose(c2, -c2[::-1, :], atol=1e-15)
     assert np.allclose(c2, c2[:, ::-1], atol=1e-15)
+
+
+@pytest.mark.parametrize("n,M,sigma", [(5, 2, 0.3), (9, 4, 0.5), (9, 6, 0.4)])
+def test_min_coefficient_at_corners_by_enumeration(n, M, sigma):
+    """The closed form c_0 - sqrt3 sum|c_k| against brute force over all 2^M corners of the xi box,
+    per cell, and no point inside the box below it."""
+    import itertools
+    coef = kl.kl_coefficients(n, M, sigma)
+    coef[0] = 1.0 + 0.3 * np.sin(np.arange(coef.shape[1]))        # a non-constant mean as well
+    r = math.sqrt(3.0)
+    corners = np.array(list(itertools.product((-r, r), repeat=M)))  # (2^M, M)
+    a_corners = coef[0][None, :] + corners @ coef[1:]               # (2^M, cells)
+    assert kl.min_coefficient_at_corners(coef) == pytest.approx(a_corners.min(), abs=1e-14)
+    inside = np.random.default_rng(3).uniform(-r, r, size=(500, M))
+    assert (coef[0][None, :] + inside @ coef[1:]).min() >= a_corners.min() - 1e-14
+    # another radius (a Hermite reference radius) scales the fluctuation part only
+    half = coef[0] - 2.0 * np.abs(coef[1:]).sum(axis=0)
+    assert kl.min_coefficient_at_corners(coef, 2.0) == pytest.approx(half.min(), abs=1e-14)
