@@ -5,14 +5,17 @@ and the SG-apply HBM bandwidth, on one GB300 (replicas on N GPUs).
 Default workload ("c3", the bandwidth-scale solve): 1025 x 1025 Q1 grid
 (1,046,529 interior nodes), M = 6 Hermite KL terms (sigma = 0.2, separable
 exponential covariance, correlation length 1), total degree p = 4 (P = 210),
-219,771,090 unknowns; FGMRES(20) with a double-float (FP64-class) Krylov basis and
-the block-triangular preconditioner whose V(1,1) cycles store their levels in BF16
-and compute in FP32 (stage right-hand sides and the preconditioned vectors z_j in
-FP32); f = 1; tolerance 1e-8 on the true relative residual, recomputed in IEEE FP64.  A step is one full solve from
-U = 0 with F resident in HBM.  Every vector is 1.76 GB (> L2), so no L2 flush
-is needed between steps.
+219,771,090 unknowns; FGMRES(20) with the Arnoldi basis, Gram-Schmidt, Givens update
+and true residual in IEEE FP64 and the block-triangular preconditioner whose V(1,1)
+cycles store their levels in BF16 and compute in FP32 (stage right-hand sides and the
+preconditioned vectors z_j in FP32); the outer operator A z_j of each Arnoldi step is
+evaluated in double-float arithmetic from the FP32 z_j and stored in FP64; f = 1;
+tolerance 1e-8 on the true relative residual, recomputed in IEEE FP64.  A step is one
+full solve from U = 0 with F resident in HBM.  Every vector is 1.76 GB (> L2), so no
+L2 flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1|c4|c5|c3s|table3]
+                    [--arith f64dfop|f64|df64] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead (see ``CpuSample``).
@@ -61,6 +64,7 @@ WORKLOADS = {
                name="sg_c5_batch64_uneven_65to513sq_M2to6_p2to4_legendre_fgmres30_fp32pc"),
 }
 PREC_NAME = {0: "f64", 1: "f32", 2: "bf16", 4: "bf16 storage, f32 output"}
+ARITH = {"f64": 0, "df64": 1, "f64dfop": 2}                     # sg_arith of include/sg.h
 ZNAME = {0: "f64", 1: "f32", 2: "bf16", 4: "f32"}              # storage of the preconditioned vectors z
 METRIC = "time to rel. residual 1e-8 (block-tri GMRES+MG) and SG-apply HBM GB/s"
 C4_METRIC = "time per adjoint gradient dJ/d(abar, sigma) (forward + transpose block-tri FGMRES+MG to 1e-8)"
@@ -151,16 +155,18 @@ def max_over_ranks(values):
     return [float(v) for v in t.cpu()]
 
 
-def build_problem(wl):
-    import numpy as np
+def build_problem(wl, h=None):
+    """KL coefficients (library host helper) and, given a handle, the device load vector
+    F = e_0 (x) h^2 f from the library (f = 1, or the seeded nodal perturbation of C2)."""
+    import torch
     from paper_1304_1755_gb300 import inputs, sg
     coef, _ = sg.sg_kl_coef(wl["n"], wl["M"], wl["sigma"])
-    n = wl["n"]
-    Nx = (n - 2) ** 2
-    P = math.comb(wl["M"] + wl["p"], wl["p"])
-    f = np.ones(Nx) if wl["f_seed"] is None else inputs.rhs_nodes(wl["f_seed"], n)
-    F = np.zeros(P * Nx)
-    F[:Nx] = f / (n - 1) ** 2           # F = e_0 (x) h^2 f  (lumped load vector)
+    if h is None:
+        return coef, None
+    f = None if wl.get("f_seed") is None else torch.as_tensor(inputs.rhs_nodes(wl["f_seed"], wl["n"])).cuda()
+    F = torch.empty(h.P * h.Nx, dtype=torch.float64, device="cuda")
+    h.rhs(F, f)
+    torch.cuda.synchronize()
     return coef, F
 
 
@@ -178,15 +184,44 @@ def terms_per_row(wl):
     return (P + 2 * M * math.comb(M + p - 1, p - 1)) / P
 
 
-def k1_flops(wl, df):
-    """Algorithmic flops of one outer-operator launch.  FP64: N (8 (1 + r) + r + 16) (corner mixing,
-    per-cell weights, element matrix and accumulation).  Double-float: the FP32 flops (add, multiply
-    = 1, fused multiply-add = 2) of the exact feature-domain scheme, 83 per coupling (exact features
-    38, three compensated products 45) plus 116 per unknown (features 32, node sums 84)."""
+def k1_method_flops(wl):
+    """The method's flops per SG apply: N (8 (1 + r) + r + 16) (corner mixing at 4 corners per
+    coupling, per-cell weight products, the Q1 element matrix and the accumulation)."""
     n = wl["n"]
     N = (n - 2) ** 2 * math.comb(wl["M"] + wl["p"], wl["p"])
-    t = terms_per_row(wl)
-    return N * (83 * t + 116) if df else N * (8 * t + (t - 1) + 16)
+    r = terms_per_row(wl) - 1
+    return N * (8 * (1 + r) + r + 16)
+
+
+def time_apply(h, X, Y, prec, reps=50, warm=5):
+    """Median CUDA-event time (ms) of one sg_apply (Y = A X), after warm-up launches."""
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warm):
+        h.apply(X, Y, prec)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        h.apply(X, Y, prec)
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def timed_solves(h, F, U, opts, steps, stream):
+    """(ms per solve, last info) of `steps` solves from U = 0, CUDA events on the solve stream."""
+    import torch
+    h.solve(F, U, **opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        info = h.solve(F, U, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, info
 
 
 def run_ours(args, wl, rank, world):
@@ -202,15 +237,16 @@ def run_ours(args, wl, rank, world):
     # a captured CUDA graph
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    coef, F_host = build_problem(wl)
+    coef, _ = build_problem(wl)
     h = sg.Handle(wl["n"], wl["M"], wl["p"], wl["family"], coef, stream=stream)
     t_tune = time.perf_counter()
     h.autotune()                          # operator tile per arithmetic (set-up, outside the timed region)
     t_tune = time.perf_counter() - t_tune
     N = h.P * h.Nx
-    F = torch.as_tensor(F_host).cuda()
+    _, F = build_problem(wl, h)
+    F_host = F.cpu()
     U = torch.zeros(N, dtype=torch.float64, device="cuda")
-    arith = sg.ARITH_DF64 if (args.arith == "df64" and wl["pc_prec"] != sg.F64) else sg.ARITH_F64
+    arith = ARITH[args.arith] if wl["pc_prec"] != sg.F64 else sg.ARITH_F64
     opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=wl["restart"], maxit=400, tol=wl["tol"],
                 pc_prec=wl["pc_prec"], reorth=0, arith=arith)
     for _ in range(args.warmup):
@@ -232,20 +268,22 @@ def run_ours(args, wl, rank, world):
     h.timing_enable(False)
     clocks = clk.summary()
     t_step = max_over_ranks([ms_total / args.steps])[0]
-    # parity at full size: independent residual check of the last solution on sampled rows is in
-    # tests/; here record the library's own recomputed FP64 residual
     its = [i.iters for i in infos]
     relres = max(i.relres_true for i in infos)
-    # SG-apply (outer FP64 operator on the BF16/FP32/FP64 preconditioned vector) per launch
-    n_k1 = max(int(phase_launches[0]), 1)                # operator launches in the timed region
-    k1_launch_ms = phase_ms[0] / max(n_k1, 1)
-    bytes_k1 = k1_bytes(wl, {0: 8, 1: 4, 2: 2, 4: 4}[wl["pc_prec"]], 8)
+    # the outer operator (dominant kernel) per launch, from the per-phase CUDA events of the timed region
+    n_k1 = max(int(phase_launches[0]), 1)
+    k1_launch_ms = phase_ms[0] / n_k1
+    zbytes = {0: 8, 1: 4, 2: 2, 4: 4}[wl["pc_prec"]]
+    ybytes = 4 * 2 if arith == sg.ARITH_DF64 else 8           # double-float w: hi + lo arrays
+    bytes_k1 = k1_bytes(wl, zbytes, ybytes)
     k1_gbs = bytes_k1 / (k1_launch_ms * 1e-3) / 1e9
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "fallback 6.8 TB/s" if peaks.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)"
+    U_ref = U.clone()
 
     # end to end through the C ABI with host (pinned) buffers, copies inside the timed region
-    Fh = torch.as_tensor(F_host).pin_memory()
+    Fh = F_host.pin_memory()
     Uh = torch.zeros(N, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     h.solve(Fh.numpy(), Uh.numpy(), **opts)      # warm-up: the first host call allocates its staging buffers
@@ -255,46 +293,46 @@ def run_ours(args, wl, rank, world):
         h.solve(Fh.numpy(), Uh.numpy(), **opts)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    del Fh, Uh
 
-    # the other preconditioner storage variants of the same solve (context for the precision choice)
+    # SG apply (K1) on its own: algorithmic bytes / median launch time, FP32 and FP64 storage
+    apply_gbs = {}
+    if not args.no_fp64_compare:
+        for name, prec, dt, sb in (("f32", sg.F32, torch.float32, 4), ("f64", sg.F64, torch.float64, 8)):
+            X = torch.rand(N, dtype=dt, device="cuda") * 2 - 1
+            Y = torch.empty_like(X)
+            ms = time_apply(h, X, Y, prec)
+            b = k1_bytes(wl, sb, sb)
+            apply_gbs[name] = {"ms": round(ms, 4), "gbs": round(b / (ms * 1e-3) / 1e9, 1),
+                               "frac_of_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4), "bytes": b,
+                               "method_tflops": round(k1_method_flops(wl) / (ms * 1e-3) / 1e12, 3)}
+            del X, Y
+
+    # the other arithmetic / storage variants of the same solve (labelled context)
     variants = {}
     if args.workload == "c3" and not args.no_fp64_compare:
-        for name, pcp in (("bf16 levels, bf16 z", sg.BF16), ("f32 levels, f32 z", sg.F32)):
-            o2 = dict(opts, pc_prec=pcp)
+        for name, o2 in (("double-float Krylov basis and Gram-Schmidt (df64), bf16 levels",
+                          dict(opts, arith=sg.ARITH_DF64)),
+                         ("f32 levels and z, f64 Krylov", dict(opts, pc_prec=sg.F32))):
             U2 = torch.zeros_like(U)
-            h.solve(F, U2, **o2)
-            torch.cuda.synchronize()
-            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e2.record(stream)
-            for _ in range(args.steps):
-                i2 = h.solve(F, U2, **o2)
-            e3.record(stream)
-            torch.cuda.synchronize()
-            variants[name] = {"ms_per_step": round(e2.elapsed_time(e3) / args.steps, 3), "iterations": i2.iters,
-                              "relres_true": i2.relres_true}
+            ms2, i2 = timed_solves(h, F, U2, o2, args.steps, stream)
+            variants[name] = {"ms_per_step": round(ms2, 3), "iterations": i2.iters, "relres_true": i2.relres_true,
+                              "solution_rel_diff_to_headline": float(torch.linalg.norm(U2 - U_ref) /
+                                                                     torch.linalg.norm(U_ref))}
             del U2
-    # the same solve in plain FP64 (FP64 preconditioner, FP64 Krylov arithmetic) on the same GPU
+    # the same solve in plain FP64 (FP64 preconditioner, FP64 Krylov arithmetic and operator)
     vs64 = None
     if not args.no_fp64_compare and (wl["pc_prec"] != sg.F64 or arith != sg.ARITH_F64):
-        opts64 = dict(opts, pc_prec=sg.F64, arith=sg.ARITH_F64)
         U64 = torch.zeros_like(U)
-        h.solve(F, U64, **opts64)
-        torch.cuda.synchronize()
-        n64 = max(1, min(args.steps, 2))
-        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2.record(stream)
-        for _ in range(n64):
-            info64 = h.solve(F, U64, **opts64)
-        e3.record(stream)
-        torch.cuda.synchronize()
-        t64 = e2.elapsed_time(e3) / n64
-        h.solve(F, U, **opts)
-        torch.cuda.synchronize()
+        t64, info64 = timed_solves(h, F, U64, dict(opts, pc_prec=sg.F64, arith=sg.ARITH_F64),
+                                   max(1, min(args.steps, 2)), stream)
         vs64 = {"ms_per_step": round(t64, 3), "iterations": info64.iters, "relres_true": info64.relres_true,
                 "speedup_of_mixed": round(t64 / t_step, 3),
-                "solution_rel_diff": float(torch.linalg.norm(U - U64) / torch.linalg.norm(U64))}
+                "solution_rel_diff": float(torch.linalg.norm(U_ref - U64) / torch.linalg.norm(U64))}
         del U64
     launches_total = sum(phase_launches)
+    kr = {sg.ARITH_F64: "f64", sg.ARITH_F64_DFOP: "f64 basis and Gram-Schmidt, double-float outer operator",
+          sg.ARITH_DF64: "df64"}[arith]
     out = {
         "metric": METRIC,
         "value": round(t_step / 1e3, 6),
@@ -306,82 +344,74 @@ def run_ours(args, wl, rank, world):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f64 storage, double-float (fp32x2) Krylov arithmetic" if arith == sg.ARITH_DF64 else "f64")
+        "dtype": {sg.ARITH_F64: "f64", sg.ARITH_F64_DFOP: "f64 Krylov (double-float outer operator)",
+                  sg.ARITH_DF64: "double-float (fp32x2) Krylov"}[arith]
                  + f", preconditioner {PREC_NAME[wl['pc_prec']]}",
         "data": "synthetic (KL coefficients of the separable exponential covariance, f = 1)",
         "config": {"workload": wl["name"], "n": wl["n"], "M": wl["M"], "p": wl["p"], "P": h.P,
                    "unknowns": N, "restart": wl["restart"], "tol": wl["tol"],
-                   "krylov_arith": "df64" if arith == sg.ARITH_DF64 else "f64",
+                   "krylov_arith": kr, "pc_prec": PREC_NAME[wl["pc_prec"]],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": (f"inputs larger than L2 ({8 * N / 1e9:.2f} GB per vector), no flush" if 8 * N > 129e6 else
                           "vectors fit in L2 (no flush: small-case timing)")},
         "iterations": its[-1],
         "relres_true": relres,
         "autotune_s": round(t_tune, 3),
-        "sg_apply_gbs": round(k1_gbs, 1),
+        "sg_apply_gbs": apply_gbs or None,
         "phases_ms_per_step": {k: round(v / args.steps, 3) for k, v in
                                zip(["operator", "preconditioner", "gram_schmidt", "other"], phase_ms)},
-        "gpu_launches": int(launches_total),
+        "gpu_launches": int(launches_total // max(args.steps, 1)),
+        "gpu_launches_timed_region": int(launches_total),
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "clocks": clocks,
         "vs_plain_fp64": vs64,
-        "preconditioner_variants": variants or None,
+        "variants": variants or None,
     }
     # C2's comparison: sigma in {0.1, 0.3, 0.5}, block-triangular vs block-diagonal, FP64 vs FP32
     # preconditioner inside FP64 flexible GMRES (one timed solve each, same grid and chaos space)
     if args.workload == "c2" and not args.no_fp64_compare:
         out["c2_sweep"] = c2_sweep(wl, stream)
-    # roofline of the dominant kernel, the outer operator (k_apply): it is bound by arithmetic
-    # (double-float: FP32 pipe; strict mode: FP64 units), not by HBM, on GB300
+    # roofline of the dominant kernel (the outer operator k_apply) by its algorithmic bytes: z read
+    # once, w written once, the coefficient rows read once
     names = ["operator", "preconditioner", "gram_schmidt", "other"]
     dom = max(range(4), key=lambda i: phase_ms[i])
-    df = arith == sg.ARITH_DF64
-    fl = k1_flops(wl, df)
-    achieved = fl / (k1_launch_ms * 1e-3) / 1e12
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if df else 1.25
+    fl = k1_method_flops(wl)
     out["roofline"] = {
-        "kernel": (f"k_apply<ArDF, {ZNAME[wl['pc_prec']]} z, double-float w> (outer SG operator)" if df else
-                   "k_apply<ArF64> (outer SG operator, FP64)"),
+        "kernel": {sg.ARITH_F64: "k_apply<ArF64> (outer SG operator, FP64)",
+                   sg.ARITH_F64_DFOP: f"k_apply<ArDF, {ZNAME[wl['pc_prec']]} z, f64 w> (outer SG operator)",
+                   sg.ARITH_DF64: f"k_apply<ArDF, {ZNAME[wl['pc_prec']]} z, double-float w> (outer SG operator)"}[arith],
         "dominant_phase": names[dom],
-        "bound": "alu",
-        "achieved": round(achieved, 2),
-        "peak": round(peak, 2),
-        "unit": "TFLOP/s",
-        "frac": round(achieved / peak, 4),
-        # DRAM bytes of one launch from the ncu capture of this kernel on the 513^2 copy of C3
-        # (profiles/k_apply_df_outer_operator_c3s_513sq_P210.md: 272.98 MB read + 391.96 MB written for
-        # 54,835,410 unknowns, 12.13 B per unknown), scaled to this workload's unknowns
-        "traffic": (round(12.126 * h.P * h.Nx) if df and wl["pc_prec"] in (sg.F32, sg.BF16Z) else None),
-        "traffic_unit": "bytes",
+        "bound": "hbm",
+        "achieved": round(k1_gbs, 1),
+        "peak": round(hbm, 1),
+        "unit": "GB/s",
+        "frac": round(k1_gbs / hbm, 4),
+        "peak_source": hbm_src,
+        "traffic": None,
+        "algorithmic_bytes_per_launch": bytes_k1,
         "launch_ms": round(k1_launch_ms, 4),
-        "flops_per_launch": fl,
-        "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock (FP32 flops of the "
-                        "double-float scheme)") if df else "nominal FP64 1.25 TFLOP/s (profiling recipe)",
-        "hbm_gbs": round(k1_gbs, 1),
-        "hbm_frac_of_measured": round(k1_gbs / hbm, 4),
+        "launches": n_k1,
+        "diagnostics": {"method_flops_per_launch": fl,
+                        "method_tflops": round(fl / (k1_launch_ms * 1e-3) / 1e12, 3),
+                        "note": "the double-float operator is bound by FP32 issue (error-free transformations), "
+                                "not by HBM; the method's own flops are the FP64 count of the operator"},
     }
     h.close()
     return out
 
 
 def c2_sweep(wl, stream):
-    import numpy as np
     import torch
     from paper_1304_1755_gb300 import sg
     rows = []
     n, M, p = wl["n"], wl["M"], wl["p"]
-    unit, _ = sg.sg_kl_coef(n, M, 1.0)
-    _, F_host = build_problem(wl)
     for sigma in (0.1, 0.3, 0.5):
-        coef = unit.copy()
-        coef[0] = 1.0
-        coef[1:] *= sigma
-        amin = float(np.min(1.0 - np.sqrt(3.0) * np.abs(coef[1:]).sum(axis=0)))
+        coef, _ = sg.sg_kl_coef(n, M, sigma)
+        amin = sg.sg_min_coef(coef, n, M)               # coercivity at the corners of the xi box
         h = sg.Handle(n, M, p, wl["family"], coef, stream=stream)
-        F = torch.as_tensor(F_host).cuda()
+        _, F = build_problem(dict(wl, sigma=sigma), h)
         for pc in (sg.PC_BLOCKTRI, sg.PC_BLOCKDIAG):
-            for pcp, ar in ((sg.F64, sg.ARITH_F64), (sg.F32, sg.ARITH_F64), (sg.F32, sg.ARITH_DF64)):
+            for pcp, ar in ((sg.F64, sg.ARITH_F64), (sg.F32, sg.ARITH_F64_DFOP), (sg.F32, sg.ARITH_F64)):
                 U = torch.zeros_like(F)
                 opts = dict(method=sg.FGMRES, precond=pc, restart=wl["restart"], maxit=400, tol=wl["tol"],
                             pc_prec=pcp, arith=ar, check=False)
@@ -395,7 +425,8 @@ def c2_sweep(wl, stream):
                 torch.cuda.synchronize()
                 rows.append({"sigma": sigma, "min_a_at_corners": round(amin, 4),
                              "precond": "block-triangular" if pc == sg.PC_BLOCKTRI else "block-diagonal",
-                             "pc_prec": {0: "f64", 1: "f32"}[pcp], "krylov": "df64" if ar else "f64",
+                             "pc_prec": {0: "f64", 1: "f32"}[pcp],
+                             "krylov": {0: "f64", 2: "f64, double-float operator"}[ar],
                              "status": info.status, "iterations": info.iters, "relres_true": info.relres_true,
                              "ms": round(e0.elapsed_time(e1), 3)})
         h.close()
@@ -423,18 +454,16 @@ def run_table3(args, wl, rank, world):
     xs = np.arange(1, n - 1) * h1 - 0.5                      # interior nodes of (-0.5, 0.5)
     X, Y = np.meshgrid(xs, xs)
     f = (2.0 * (0.5 - X ** 2 - Y ** 2)).reshape(-1)
-    unit, _ = sg.sg_kl_coef(n, M, 1.0)
+    fdev = torch.as_tensor(f).cuda()
     methods = [("Block-GS", sg.BGS, sg.PC_BLOCKTRI), ("BD-PCG", sg.PCG, sg.PC_BLOCKDIAG),
                ("BT-GPCG", sg.GPCG, sg.PC_BLOCKTRI), ("BT-GMRes", sg.GMRES, sg.PC_BLOCKTRI),
                ("BS-PCG", sg.PCG, sg.PC_BLOCKSYM)]
     rows, total_ms = [], 0.0
     for si, sigma in enumerate(wl["sigmas"]):
-        coef = unit.copy()
-        coef[0] = 1.0
-        coef[1:] *= sigma
+        coef, _ = sg.sg_kl_coef(n, M, sigma)
         h = sg.Handle(n, M, p, wl["family"], coef, nu1=wl["nu"], nu2=wl["nu"], stream=stream)
-        F = torch.zeros(h.P * h.Nx, dtype=torch.float64, device="cuda")
-        F[:h.Nx] = torch.as_tensor(f * h1 * h1)
+        F = torch.empty(h.P * h.Nx, dtype=torch.float64, device="cuda")
+        h.rhs(F, fdev)
         for name, meth, pc in methods:
             U = torch.zeros_like(F)
             o = dict(method=meth, precond=pc, restart=wl["restart"], maxit=1000, tol=wl["tol"], pc_prec=sg.F64,
@@ -462,38 +491,34 @@ def run_table3(args, wl, rank, world):
 
 
 def c4_cpu_sample(wl, warmup=0, steps=1):
-    """The oracle (as it stands) computing the same gradient on the 129 x 129 copy of the C4 problem:
-    block-triangular FGMRES forward solve, the transposed solve with the upper sweep, J and both
-    gradients; scaled to the workload by unknowns.  Returns (seconds, description)."""
-    from oracle import adjoint as oadj, kl, krylov, mg, precond, sg as osg
+    """The oracle computing the same gradient on the 129 x 129 copy of the C4 problem: the C/OpenMP
+    block-triangular FGMRES forward solve, the transposed solve with the upper sweep, then J and both
+    gradients by the Python oracle; scaled to the workload by unknowns.  Returns (seconds,
+    description, threads)."""
+    from oracle import adjoint as oadj, csolver, kl, mg, sg as osg
     from paper_1304_1755_gb300 import inputs
     nc = 129
     unit = kl.kl_coefficients(nc, wl["M"], 1.0)
-    coef = unit.copy()
-    coef[0] = inputs.lognormal_cells(wl["abar_seed"], nc, 0.2)
-    coef[1:] *= wl["sigma"]
+    coef = kl.kl_coefficients(nc, wl["M"], wl["sigma"], abar=inputs.lognormal_cells(wl["abar_seed"], nc, 0.2))
     sysm = osg.build(nc, wl["M"], wl["p"], wl["family"], coef)
-    A = osg.assemble(sysm)
     F = osg.rhs(sysm)
-    solver = precond.DiagSolver(sysm.K[0], mg.Hierarchy(sysm.K[0], nc))
+    c = csolver.CSolver(sysm, mg.Hierarchy(sysm.K[0], nc))
     times, its = [], (0, 0)
     for k in range(warmup + steps):
         t0 = time.perf_counter()
-        U, i1, _ = krylov.gmres(lambda v: A @ v, lambda r: precond.block_tri_inv(sysm, solver, r), F,
-                                tol=wl["tol"], restart=wl["restart"], maxit=400, flexible=True)
+        U, i1, _, _, _ = c.fgmres(F, restart=wl["restart"], maxit=400, tol=wl["tol"])
         _, gU = oadj.objective(sysm, U)
-        Lam, i2, _ = krylov.gmres(lambda v: A.T @ v,
-                                  lambda r: precond.block_tri_inv(sysm, solver, r, transpose=True), gU,
-                                  tol=wl["tol"], restart=wl["restart"], maxit=400, flexible=True)
+        Lam, i2, _, _, _ = c.fgmres(gU, restart=wl["restart"], maxit=400, tol=wl["tol"], transpose=True)
         oadj.gradients(sysm, U, Lam, unit)
         if k >= warmup:
             times.append(time.perf_counter() - t0)
         its = (i1, i2)
     N = (wl["n"] - 2) ** 2 * math.comb(wl["M"] + wl["p"], wl["p"])
     t = statistics.median(times)
-    return t * N / (sysm.P * sysm.Nx), (f"oracle gradient (BT-FGMRES forward {its[0]} and transposed {its[1]} "
-                                        f"iterations, J, both gradients) on the {nc}x{nc} copy "
-                                        f"({sysm.P * sysm.Nx} unknowns) in {t:.2f} s; scaled by unknowns")
+    return t * N / (sysm.P * sysm.Nx), (f"oracle gradient (C/OpenMP BT-FGMRES forward {its[0]} and transposed "
+                                        f"{its[1]} iterations, J and both gradients in the Python oracle) on the "
+                                        f"{nc}x{nc} copy ({sysm.P * sysm.Nx} unknowns) in {t:.2f} s; scaled by "
+                                        f"unknowns"), csolver.threads()
 
 
 def run_c4(args, wl, rank, world):
@@ -511,18 +536,15 @@ def run_c4(args, wl, rank, world):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     n, M, p = wl["n"], wl["M"], wl["p"]
-    unit, _ = sg.sg_kl_coef(n, M, 1.0)
-    coef = unit.copy()
-    coef[0] = inputs.lognormal_cells(wl["abar_seed"], n, 0.2)
-    coef[1:] *= wl["sigma"]
+    coef, _ = sg.sg_kl_coef(n, M, wl["sigma"], abar=inputs.lognormal_cells(wl["abar_seed"], n, 0.2))
     h = sg.Handle(n, M, p, wl["family"], coef, stream=stream)
     N = h.P * h.Nx
-    F = torch.zeros(N, dtype=torch.float64, device="cuda")
-    F[:h.Nx] = 1.0 / (n - 1) ** 2
+    F = torch.empty(N, dtype=torch.float64, device="cuda")
+    h.rhs(F)
     U, G, Lam = torch.zeros_like(F), torch.empty_like(F), torch.zeros_like(F)
     g_abar = torch.empty((n - 1) ** 2, dtype=torch.float64, device="cuda")
     opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=wl["restart"], maxit=400, tol=wl["tol"],
-                pc_prec=wl["pc_prec"], reorth=0, arith=sg.ARITH_DF64)
+                pc_prec=wl["pc_prec"], reorth=0, arith=sg.ARITH_F64_DFOP)
 
     def gradient():
         fi = h.solve(F, U, **opts)
@@ -574,7 +596,7 @@ def run_c4(args, wl, rank, world):
         "metric": C4_METRIC,
         "value": round(t_step / 1e3, 6), "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_step, 3), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 storage, double-float Krylov arithmetic, preconditioner f32",
+        "dtype": "f64 Krylov (double-float outer operator), preconditioner f32",
         "data": "synthetic (lognormal mean coefficient seed 2, KL modes, f = 1)",
         "config": {"workload": wl["name"], "unknowns": N, "parameters": (n - 1) ** 2 + 1,
                    "l2": "vectors fit in L2 (no flush: small-case timing)"},
@@ -593,22 +615,18 @@ def run_c4(args, wl, rank, world):
 
 def c5_systems(wl):
     """The uneven batch: per system (n, M, p, sigma) from the seeded recipe; sigma is lowered where
-    needed so that the coefficient stays >= 0.05 at every corner of the xi box (Legendre:
-    abar - sqrt(3) sum_k |c_k| >= 0.05 per cell)."""
+    needed so that the coefficient stays >= 0.05 at every corner of the xi box (the library's
+    sg_min_coef of the unit-sigma fluctuation gives the bound)."""
     import numpy as np
     from paper_1304_1755_gb300 import inputs, sg
     out = []
     for s in inputs.batch_systems(wl["batch_seed"], wl["count"]):
-        unit, _ = sg.sg_kl_coef(s["n"], s["M"], 1.0)
-        worst = float(np.max(np.sqrt(3.0) * np.abs(unit[1:]).sum(axis=0)))
+        n, M = s["n"], s["M"]
+        unit, _ = sg.sg_kl_coef(n, M, 1.0, abar=np.zeros((n - 1) ** 2))
+        worst = -sg.sg_min_coef(unit, n, M)             # max over cells of sqrt3 sum_k |c_k| at sigma = 1
         sigma = min(s["sigma"], 0.95 / worst)
-        coef = unit.copy()
-        coef[0] = 1.0
-        coef[1:] *= sigma
-        n = s["n"]
-        F = np.zeros(math.comb(s["M"] + s["p"], s["p"]) * (n - 2) ** 2)
-        F[:(n - 2) ** 2] = 1.0 / (n - 1) ** 2
-        out.append(dict(s, sigma=sigma, sigma_drawn=s["sigma"], coef=coef, F=F))
+        coef, _ = sg.sg_kl_coef(n, M, sigma)
+        out.append(dict(s, sigma=sigma, sigma_drawn=s["sigma"], coef=coef))
     return out
 
 
@@ -630,11 +648,15 @@ def run_c5(args, wl, rank, world):
     for h in hs:
         h.autotune()
     tune_s = time.perf_counter() - t0
-    Fs = [torch.as_tensor(s["F"]).cuda() for s in systems]
+    Fs = []
+    for h in hs:
+        F = torch.empty(h.P * h.Nx, dtype=torch.float64, device="cuda")
+        h.rhs(F)
+        Fs.append(F)
     Us = [torch.zeros_like(F) for F in Fs]
     unknowns = sum(int(F.numel()) for F in Fs)
     opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=wl["restart"], maxit=400, tol=wl["tol"],
-                pc_prec=wl["pc_prec"], reorth=0, arith=sg.ARITH_F64)
+                pc_prec=wl["pc_prec"], reorth=0, arith=sg.ARITH_F64_DFOP)
 
     def one_at_a_time():
         return [h.solve(F, U, **opts) for h, F, U in zip(hs, Fs, Us)]
@@ -670,7 +692,7 @@ def run_c5(args, wl, rank, world):
     op_ms = sum(m[0] for m, _ in ph) / args.steps
     op_launches = sum(l[0] for _, l in ph) // args.steps
     # end to end through the C ABI with host (pinned) buffers: sg_solve stages them per system
-    Fh = [torch.as_tensor(s["F"]).pin_memory() for s in systems]
+    Fh = [F.cpu().pin_memory() for F in Fs]
     Uh = [torch.zeros_like(F).pin_memory() for F in Fh]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -685,7 +707,7 @@ def run_c5(args, wl, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_batch * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 Krylov, preconditioner f32",
+        "dtype": "f64 Krylov (double-float outer operator), preconditioner f32",
         "data": "synthetic (seeded uneven batch: KL coefficients, Legendre chaos, f = 1)",
         "config": {"workload": wl["name"], "systems": len(hs), "unknowns": unknowns, "nstreams": wl["nstreams"],
                    "sigma_lowered": sum(1 for s in systems if s["sigma"] < s["sigma_drawn"]),
@@ -702,88 +724,103 @@ def run_c5(args, wl, rank, world):
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "clocks": clocks,
     }
-    fl = sum(k1_flops(dict(n=s["n"], M=s["M"], p=s["p"]), False) for s in systems)   # one apply per system
+    # the outer operator (double-float arithmetic, FP32 z in, FP64 w out): one apply per system, bytes
+    # by the algorithmic count of each system, time = the mean event-timed launch over the batch
+    byt = sum(k1_bytes(dict(n=s["n"], M=s["M"], p=s["p"]), 4, 8) for s in systems)
     apply_ms = op_ms / max(op_launches, 1) * len(hs)
-    out["roofline"] = {"kernel": "k_apply<ArF64> (outer SG operator, FP64), summed over the batch's systems",
-                       "bound": "alu", "achieved": round(fl / (apply_ms * 1e-3) / 1e12, 3), "peak": 1.25,
-                       "unit": "TFLOP/s", "frac": round(fl / (apply_ms * 1e-3) / 1e12 / 1.25, 4), "traffic": None,
-                       "peak_source": "nominal FP64 1.25 TFLOP/s (profiling recipe)",
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    out["roofline"] = {"kernel": "k_apply<ArDF, f32 z, f64 w> (outer SG operator), summed over the batch's systems",
+                       "bound": "hbm", "achieved": round(byt / (apply_ms * 1e-3) / 1e9, 1), "peak": hbm,
+                       "unit": "GB/s", "frac": round(byt / (apply_ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
                        "note": "launch time measured per system with events; concurrent streams overlap"}
     for h in hs:
         h.close()
     return out
 
 
+def _cores_c():
+    from oracle import csolver
+    return csolver.threads()
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 class CpuSampleBatch:
-    """The oracle on a bounded sample of the uneven batch: its systems on the 65 x 65 grid, solved
-    one after another by the oracle's block-triangular FGMRES, until about 20 s have been spent;
-    the metric is unknowns solved per second."""
+    """The oracle's C/OpenMP BT-FGMRES on a bounded sample of the uneven batch: its systems on
+    the 65 x 65 grid, solved one after another until about 20 s have been spent; the metric is
+    unknowns solved per second."""
 
     def __init__(self, wl, budget_s=20.0):
-        from oracle import mg, precond, sg as osg
+        from oracle import csolver, mg, sg as osg
         self.wl, self.budget_s = wl, budget_s
         self.items = []
         for s in c5_systems(wl):
             if s["n"] != 65:
                 continue
             sysm = osg.build(s["n"], s["M"], s["p"], wl["family"], s["coef"])
-            A = osg.assemble(sysm)
-            solver = precond.DiagSolver(sysm.K[0], mg.Hierarchy(sysm.K[0], s["n"]))
-            self.items.append((sysm, A, osg.rhs(sysm), solver))
+            c = csolver.CSolver(sysm, mg.Hierarchy(sysm.K[0], s["n"]))
+            self.items.append((sysm, c, osg.rhs(sysm)))
 
     def run(self):
-        from oracle import krylov, precond
         t0 = time.perf_counter()
         done = 0
         count = 0
-        for sysm, A, F, solver in self.items:
-            krylov.gmres(lambda v: A @ v, lambda r: precond.block_tri_inv(sysm, solver, r), F, tol=self.wl["tol"],
-                         restart=self.wl["restart"], maxit=400, flexible=True)
+        for sysm, c, F in self.items:
+            c.fgmres(F, restart=self.wl["restart"], maxit=400, tol=self.wl["tol"])
             done += sysm.P * sysm.Nx
             count += 1
             if time.perf_counter() - t0 > self.budget_s:
                 break
         dt = time.perf_counter() - t0
-        return done / dt, f"oracle BT-FGMRES({self.wl['restart']}) to {self.wl['tol']:g} on {count} of the batch's " \
-                          f"65x65 systems ({done} unknowns) in {dt:.1f} s, one after another"
+        return done / dt, (f"oracle C/OpenMP BT-FGMRES({self.wl['restart']}) to {self.wl['tol']:g} on {count} of "
+                           f"the batch's 65x65 systems ({done} unknowns) in {dt:.1f} s, one after another")
 
 
 class CpuSample:
-    """The oracle (as it stands, single-threaded scipy sparse kernels) on a bounded sample of the
-    workload: the same M, p, family, sigma, restart and tolerance on a smaller grid copy
-    (129 x 129 for the large workloads), a full block-triangular FGMRES solve from U = 0.
-    Multigrid-preconditioned iteration counts do not grow with the grid, so the sample is scaled
-    to the workload by its time per (unknown x iteration)."""
+    """The oracle's plain C/OpenMP FP64 BT-FGMRES + V(1,1) (oracle/csolve.c, the Python oracle's
+    matrices, all host cores) on a bounded sample of the workload: the same M, p, family, sigma,
+    right-hand side, restart and tolerance, a full solve from U = 0, on the workload's own grid
+    when it has at most 513^2 vertices (C2: timed in full) and on the 513^2 copy otherwise (C3),
+    scaled to the workload by unknowns (multigrid-preconditioned iteration counts do not grow
+    with the grid)."""
 
     def __init__(self, wl):
-        from oracle import kl, mg, precond, sg as osg
-        self.n = min(wl["n"], 129)
+        from oracle import csolver, kl, mg, sg as osg
+        from paper_1304_1755_gb300 import inputs
+        self.n = min(wl["n"], 513)
         self.wl = wl
         t0 = time.perf_counter()
         coef = kl.kl_coefficients(self.n, wl["M"], wl["sigma"])
         self.s = osg.build(self.n, wl["M"], wl["p"], wl["family"], coef)
-        self.A = osg.assemble(self.s)
-        self.F = osg.rhs(self.s)
-        self.solver = precond.DiagSolver(self.s.K[0], mg.Hierarchy(self.s.K[0], self.n))
+        f = None if wl.get("f_seed") is None or self.n != wl["n"] else inputs.rhs_nodes(wl["f_seed"], self.n)
+        self.F = osg.rhs(self.s, f)
+        self.c = csolver.CSolver(self.s, mg.Hierarchy(self.s.K[0], self.n))
+        self.cores = csolver.threads()
         self.setup_s = time.perf_counter() - t0
 
     def run(self):
         """One full solve; returns (seconds, iterations)."""
-        from oracle import krylov, precond
-        s, A = self.s, self.A
-        t0 = time.perf_counter()
-        _, its, _ = krylov.gmres(lambda v: A @ v, lambda r: precond.block_tri_inv(s, self.solver, r), self.F,
-                                 tol=self.wl["tol"], restart=self.wl["restart"], maxit=400, flexible=True)
-        return time.perf_counter() - t0, max(its, 1)
+        _, its, rr, rc, dt = self.c.fgmres(self.F, restart=self.wl["restart"], maxit=400, tol=self.wl["tol"])
+        self.relres = rr
+        return dt, max(its, 1)
 
     @property
     def unknowns(self):
         return self.s.P * self.s.Nx
 
+    def scaled(self, dt, unknowns):
+        return dt * unknowns / self.unknowns
+
     def describe(self, dt, its):
-        return (f"oracle BT-FGMRES({self.wl['restart']}) to {self.wl['tol']:g} on the {self.n}x{self.n} copy "
-                f"(P={self.s.P}, {self.unknowns} unknowns): {its} iterations in {dt:.1f} s "
-                f"(+{self.setup_s:.1f} s set-up); scaled by unknowns x iterations")
+        where = "the workload itself" if self.n == self.wl["n"] else f"the {self.n}x{self.n} copy, scaled by unknowns"
+        return (f"oracle C/OpenMP FP64 BT-FGMRES({self.wl['restart']}) + V(1,1) to {self.wl['tol']:g} on {where} "
+                f"(P={self.s.P}, {self.unknowns} unknowns): {its} iterations in {dt:.2f} s on {self.cores} threads "
+                f"(+{self.setup_s:.1f} s set-up by the Python oracle)")
 
 
 def main():
@@ -793,7 +830,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--arith", default="df64", choices=["f64", "df64"])
+    ap.add_argument("--arith", default="f64dfop", choices=sorted(ARITH))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--pc-prec", choices=["f64", "f32", "bf16", "bf16z"], default=None,
@@ -812,16 +849,16 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": f"{args.workload} is a context/profiling workload "
                                                                    "without a reference timing"}))
             return
+        common = {"impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                  "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                  "config": {"workload": wl["name"]}}
         if args.workload == "c4":
-            v, sample = c4_cpu_sample(wl, args.warmup, args.steps)
-            print(json.dumps({"impl": "reference", "metric": C4_METRIC, "value": round(v, 3), "unit": "s",
-                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
-                              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                              "config": {"workload": wl["name"]},
-                              "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
-                                               "sample": sample},
-                              "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
-                                      "d2h_bytes_per_step": 0}}))
+            v, sample, cores = c4_cpu_sample(wl, args.warmup, args.steps)
+            print(json.dumps(dict(common, metric=C4_METRIC, value=round(v, 3), unit="s", higher_is_better=False,
+                                  cpu_baseline={"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
+                                                "sample": sample},
+                                  e2e={"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0})))
             return
         if args.workload == "c5":
             smp = CpuSampleBatch(wl)
@@ -831,14 +868,11 @@ def main():
                 if k >= args.warmup:
                     vals.append(v)
             v = statistics.median(vals)
-            print(json.dumps({"impl": "reference", "metric": C5_METRIC, "value": round(v, 1), "unit": "unknowns/s",
-                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                              "config": {"workload": wl["name"]},
-                              "cpu_baseline": {"value": round(v, 1), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                                               "sample": sample},
-                              "e2e": {"value": round(v, 1), "unit": "unknowns/s", "h2d_bytes_per_step": 0,
-                                      "d2h_bytes_per_step": 0}}))
+            print(json.dumps(dict(common, metric=C5_METRIC, value=round(v, 1), unit="unknowns/s", higher_is_better=True,
+                                  cpu_baseline={"value": round(v, 1), "unit": "unknowns/s", "cores": _cores_c(),
+                                                "kind": "oracle", "sample": sample},
+                                  e2e={"value": round(v, 1), "unit": "unknowns/s", "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0})))
             return
         smp = CpuSample(wl)
         times = []
@@ -848,17 +882,16 @@ def main():
                 times.append(dt)
         n, P = wl["n"], math.comb(wl["M"] + wl["p"], wl["p"])
         unknowns = (n - 2) ** 2 * P
-        # the oracle's own iteration count at the copy, scaled to the workload's unknowns
-        v = statistics.median(times) * unknowns / smp.unknowns
-        sample = smp.describe(statistics.median(times), its)
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": world,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
-                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic (KL coefficients of the separable exponential covariance, f = 1)",
-                          "config": {"workload": wl["name"], "unknowns": unknowns},
-                          "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
-                                           "sample": sample},
-                          "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        dt = statistics.median(times)
+        v = smp.scaled(dt, unknowns)
+        print(json.dumps(dict(common, metric=METRIC, value=round(v, 3), unit="s", ms_per_step=round(v * 1e3, 1),
+                              higher_is_better=False,
+                              data="synthetic (KL coefficients of the separable exponential covariance, f = 1)",
+                              config={"workload": wl["name"], "unknowns": unknowns},
+                              cpu_baseline={"value": round(v, 3), "unit": "s", "cores": smp.cores, "kind": "oracle",
+                                            "sample": smp.describe(dt, its)},
+                              e2e={"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                                   "d2h_bytes_per_step": 0})))
         return
     if world > 1:
         import torch
@@ -873,8 +906,9 @@ def main():
     if args.workload == "c4":
         out = run_c4(args, wl, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            v, sample = c4_cpu_sample(wl)
-            out["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+            v, sample, cores = c4_cpu_sample(wl)
+            out["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
+                                   "sample": sample}
         if rank == 0:
             print(json.dumps(out))
         if world > 1:
@@ -884,7 +918,7 @@ def main():
         out = run_c5(args, wl, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             v, sample = CpuSampleBatch(wl).run()
-            out["cpu_baseline"] = {"value": round(v, 1), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+            out["cpu_baseline"] = {"value": round(v, 1), "unit": "unknowns/s", "cores": _cores_c(), "kind": "oracle",
                                    "sample": sample}
         if rank == 0:
             print(json.dumps(out))
@@ -895,10 +929,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = CpuSample(wl)
         dt, its = smp.run()
-        v = dt / (smp.unknowns * its) * out["config"]["unknowns"] * out["iterations"]
-        out["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
-                               "sample": smp.describe(dt, its) + f" x {out['iterations']} GPU iterations "
-                                                                 f"(extrapolated)"}
+        v = smp.scaled(dt, out["config"]["unknowns"])
+        out["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": smp.cores, "kind": "oracle",
+                               "sample": smp.describe(dt, its), "host_cores": _host_cores()}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

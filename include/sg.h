@@ -60,13 +60,20 @@ typedef enum {
  * in FP32 avoids the BF16 rounding of the flexible basis z_j, which costs FGMRES
  * extra iterations, while the multigrid traffic stays at BF16 width. */
 typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2, SG_DF64 = 3, SG_BF16Z = 4 } sg_prec;
-/* Arithmetic of the outer Krylov solver: SG_ARITH_F64 = IEEE FP64 throughout;
- * SG_ARITH_DF64 = the Arnoldi basis, the outer operator A z and the
- * Gram-Schmidt sums in double-float (FP32 pairs with error-free
- * transformations), the Givens/least-squares update on the host in FP64 and
- * the final true residual recomputed in IEEE FP64 (FGMRES only; the
- * preconditioner must then be SG_F32 or SG_BF16). */
-typedef enum { SG_ARITH_F64 = 0, SG_ARITH_DF64 = 1 } sg_arith;
+/* Arithmetic of the outer Krylov solver (the preconditioner's own arithmetic is set by pc_prec):
+ *   SG_ARITH_F64: IEEE FP64 throughout -- Arnoldi basis, outer operator A z_j,
+ *     Gram-Schmidt, Givens/least-squares update and true residual.
+ *   SG_ARITH_F64_DFOP: as SG_ARITH_F64 (FP64 basis, FP64 Gram-Schmidt, FP64 Givens
+ *     update on the host, IEEE FP64 true residual at every restart and at the end),
+ *     except that the outer operator w = A z_j of each Arnoldi step is evaluated in
+ *     double-float arithmetic (FP32 pairs with error-free transformations, about 48
+ *     significant bits; the FP32/BF16 z_j are exact in it) and w is rounded to FP64 on
+ *     the store.  GMRES/FGMRES with an SG_F32, SG_BF16 or SG_BF16Z preconditioner.
+ *   SG_ARITH_DF64: the Arnoldi basis, the outer operator and the Gram-Schmidt sums
+ *     in double-float (48-bit significand, FP32 exponent range); the Givens update on
+ *     the host in FP64; every true residual (restart and final) in IEEE FP64.
+ *     FGMRES with an SG_F32, SG_BF16 or SG_BF16Z preconditioner. */
+typedef enum { SG_ARITH_F64 = 0, SG_ARITH_DF64 = 1, SG_ARITH_F64_DFOP = 2 } sg_arith;
 typedef enum { SG_LEGENDRE = 0, SG_HERMITE = 1 } sg_family;
 /* SG_BGS: the stationary block Gauss-Seidel iteration U += B_T^{-1}(F - A U) (Sec. 4.2). */
 typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3, SG_BGS = 4 } sg_method;
@@ -95,13 +102,14 @@ typedef struct {
 /* Solver options (Sec. 4.2, 6).  method: GMRES (right preconditioned) or
  * FGMRES (flexible: stores z_j = B^{-1} v_j in pc_prec) or GPCG[1] or PCG.
  * precond: block-triangular B_T, block-diagonal B_D or none.  restart: Krylov
- * dimension m of (F)GMRES(m) (1..64).  maxit: maximum preconditioner
+ * dimension m of (F)GMRES(m) (1..32).  maxit: maximum preconditioner
  * applications.  tol: stop when ||F - A U||_2 / ||F||_2 <= tol (true residual,
  * recomputed in FP64 at every restart and at the end).  pc_prec: precision of
- * the preconditioner (V-cycle and triangular sweep); the outer Krylov vectors,
- * orthogonalisation, Givens rotations, true residual and coarsest-grid solve
- * are always FP64 (SG_F64, SG_F32, SG_BF16 or SG_BF16Z; z_j is stored in FP32 for
- * SG_BF16Z).  transpose: solve A^T U = F preconditioned by B^T (the
+ * the preconditioner (V-cycle and triangular sweep: SG_F64, SG_F32, SG_BF16 or
+ * SG_BF16Z; z_j is stored in FP32 for SG_BF16Z); the coarsest-grid solve is FP64 in
+ * every mode.  The arithmetic of the outer Krylov vectors, operator and
+ * orthogonalisation is chosen by arith (sg_arith above); the Givens rotations and
+ * the true residual are FP64 in every mode.  transpose: solve A^T U = F preconditioned by B^T (the
  * adjoint solve; B_T^T is the upper block-triangular sweep).  x0_given: U holds
  * an initial guess (else U = 0 is used).  reorth: 0 classical Gram-Schmidt,
  * 1 classical Gram-Schmidt with a second pass when the norm drops by more than
@@ -143,6 +151,16 @@ typedef struct {
 int sg_kl_coef(int n, int M, double sigma, double corr_len, const double* abar,
                double* coef_out, double* lambda_out);
 
+/* Host helper, coercivity check of a coefficient set (Sec. 2.1: the paper's
+ * assumption that a stays above a positive constant, and its remark that the
+ * truncated expansion can violate it): *amin_out = min over the (n-1)^2 cells of
+ * min_{|xi_k| <= xi_max} a(x_e, xi) = coef[0][e] - xi_max sum_{k>=1} |coef[k][e]|
+ * (a is linear in xi, so the minimum is at a corner of the box).  xi_max = sqrt(3)
+ * is the support of the Legendre chaos variables; Hermite variables are unbounded,
+ * so there xi_max is a reference radius chosen by the caller.  coef as in sg_problem
+ * (host, (M+1) x (n-1)^2).  Pure host computation, no device use. */
+int sg_min_coef(int n, int M, const double* coef, double xi_max, double* amin_out);
+
 /* Build a handle: uploads coefficients, basis tables and the multigrid
  * hierarchy (Galerkin coarse stencils when abar is not constant 1).  stream is
  * a cudaStream_t (NULL = legacy default stream). */
@@ -156,6 +174,14 @@ int sg_sizes(sg_handle h, int* Nx, int* P, int* nlevels);
 /* Multi-indices of the PC basis (host array P x M, row i = alpha_i),
  * degree-graded order (Sec. 3.3). */
 int sg_basis(sg_handle h, int* alpha);
+
+/* Load vector of the SG system (Eq. tensor-product's right-hand side): f is
+ * deterministic, so only the mean PC block is nonzero, F = e_0 (x) F_0, with the
+ * lumped Q1 load F_0[s] = h^2 f_s (h = 1/(n-1); exact for constant f).  f_nodes: the
+ * N_x interior nodal values of f (device, FP64), or NULL for f = 1.  F: device,
+ * FP64, P * N_x values, fully overwritten (the blocks i >= 1 are set to zero).
+ * Stream-ordered on the handle's stream; returns before the kernel finishes. */
+int sg_rhs(sg_handle h, const double* f_nodes, double* F);
 
 /* Y = A X (Eq. tensor-product), device X, Y in precision prec; arithmetic in
  * FP64 for SG_F64, double-float for SG_DF64, FP32 otherwise. */
@@ -178,7 +204,8 @@ int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec);
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec);
 /* sg_vcycle without any device allocation (the paper has no counterpart: this is a
  * library-usage variant of the V-cycle of Sec. 4.1).  Same arguments and result as
- * sg_vcycle, but the coarse-level buffers come from one fixed 32 MiB array compiled
+ * sg_vcycle for prec = SG_F64, SG_F32 or SG_BF16 (other precisions return SG_E_ARG),
+ * but the coarse-level buffers come from one fixed 32 MiB array compiled
  * into the library instead of the handle's workspace, which sg_vcycle allocates on
  * its first call.  It is meant for callers that must not allocate: code running
  * under a caching allocator that already holds the device's free memory, or inside

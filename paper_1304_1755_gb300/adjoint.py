@@ -9,7 +9,6 @@ with ``sg_adjoint_gradients``.  Every step runs in the library's kernels; this m
 only marshals tensors.  abar is the per-cell mean coefficient ((n-1)^2 values), sigma the
 standard deviation that scales the unit-variance KL modes.
 """
-import numpy as np
 import torch
 
 from . import sg
@@ -19,15 +18,15 @@ class SGObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, abar, sigma, spec):
         n, M, p, family = spec["n"], spec["M"], spec["p"], spec["family"]
-        unit = spec["unit_coef"]                       # (M+1, Nc) KL coefficients at sigma = 1 (row 0 unused)
-        coef = np.empty_like(unit)
-        coef[0] = abar.detach().to("cpu", torch.float64).numpy()
-        coef[1:] = float(sigma) * unit[1:]
+        # coefficients (sg_kl_coef: row 0 = abar, rows k >= 1 = sigma sqrt(lambda_k) b_k) and the load
+        # vector (sg_rhs) come from the library; abar crosses to the host because sg_kl_coef is host code
+        coef, _ = sg.sg_kl_coef(n, M, float(sigma), spec.get("corr_len", 1.0),
+                                abar=abar.detach().to("cpu", torch.float64).numpy())
         stream = torch.cuda.current_stream()
         h = sg.Handle(n, M, p, family, coef, stream=stream)
         N = h.P * h.Nx
-        F = torch.zeros(N, dtype=torch.float64, device=abar.device)
-        F[:h.Nx] = 1.0 / (n - 1) ** 2 if spec.get("f") is None else spec["f"]
+        F = torch.empty(N, dtype=torch.float64, device=abar.device)
+        h.rhs(F, spec.get("f"))
         U = torch.zeros_like(F)
         opts = dict(method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=spec.get("restart", 30),
                     tol=spec.get("tol", 1e-10), pc_prec=spec.get("pc_prec", sg.F64), maxit=spec.get("maxit", 500))
@@ -53,7 +52,7 @@ class SGObjective(torch.autograd.Function):
 
 def objective(abar, sigma, n, M, p, family=sg.LEGENDRE, corr_len=1.0, **opts):
     """J(abar, sigma) as a differentiable scalar (abar: cuda float64 tensor of (n-1)^2 cells,
-    sigma: 0-d float64 tensor)."""
-    unit, _ = sg.sg_kl_coef(n, M, 1.0, corr_len)
-    spec = dict(n=n, M=M, p=p, family=family, unit_coef=unit, **opts)
+    sigma: 0-d float64 tensor).  opts: restart, tol, pc_prec, maxit, and f (device FP64 values of
+    f at the (n-2)^2 interior nodes; f = 1 when absent)."""
+    spec = dict(n=n, M=M, p=p, family=family, corr_len=corr_len, **opts)
     return SGObjective.apply(abar, sigma, spec)

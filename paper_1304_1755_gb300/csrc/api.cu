@@ -209,6 +209,7 @@ struct OpsF64 {
   const double* F;
   double* U;
   bool flexible;
+  bool dfop;       // the outer operator A z_j in double-float arithmetic (FP32/BF16 z_j, FP64 result)
   double* V;
   int init() {
     int rc = ensure_krylov(h, o.restart + 1, flexible ? o.restart : 1, zprec_of(o.pc_prec), 0);
@@ -220,13 +221,22 @@ struct OpsF64 {
   int norm2_rhs(double* out) { int rc; *out = host_dot(h, F, F, N, &rc); return rc; }
   int zero_solution() { return vec_fill(h, U, N, 0.0); }
   int residual(bool u_zero) {
+    if (u_zero) {                                               // F - A 0 = F: no operator pass
+      SG_CUDA(h, cudaMemcpyAsync(v(0), F, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+      return SG_OK;
+    }
     int rc;
-    if (!u_zero && (rc = spec_copy_u(h, U, N))) return rc;      // U is final if this check converges
+    if ((rc = spec_copy_u(h, U, N))) return rc;                 // U is final if this check converges
     return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F);
   }
   int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
   int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
-  int apply(int j) { return apply_f64(h, 0, zprec_of(o.pc_prec), z(j), SG_F64, v(j + 1), nullptr); }
+  int apply(int j) {
+    if (dfop)    // FP32-class z_j is exact in double-float; w is rounded once to FP64 on the store
+      return launch_apply(h, 0, zprec_of(o.pc_prec), z(j), 0, SG_F64, v(j + 1), 0, SG_F64, nullptr, 0, 0, h->P, 0, 0,
+                          SG_DF64);
+    return apply_f64(h, 0, zprec_of(o.pc_prec), z(j), SG_F64, v(j + 1), nullptr);
+  }
   int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
   int axpys(int j, const double* c) { return vec_axpys_norm(h, V, h->Np, j + 1, c, v(j + 1), h->Np, nullptr); }
   int update(int k, const double* y) {
@@ -438,7 +448,7 @@ int solve_gmres(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, s
     OpsDF ops{h, o, N, F, U, nullptr, nullptr, nullptr};
     return solve_gmres_t(h, ops, o, info);
   }
-  OpsF64 ops{h, o, N, F, U, flexible, nullptr};
+  OpsF64 ops{h, o, N, F, U, flexible, o.arith == SG_ARITH_F64_DFOP, nullptr};
   return solve_gmres_t(h, ops, o, info);
 }
 
@@ -598,6 +608,16 @@ int sg_fail(sg_ctx* h, int code, const std::string& msg) {
   return code;
 }
 
+int sg_check_device(sg_ctx* h, const char* who) {
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return sg_fail(h, SG_E_CUDA, std::string(who) + ": cudaGetDevice: " + cudaGetErrorString(e));
+  if (dev != h->device)
+    return sg_fail(h, SG_E_STATE, std::string(who) + ": the handle belongs to device " + std::to_string(h->device) +
+                                      " but device " + std::to_string(dev) + " is current");
+  return SG_OK;
+}
+
 size_t prec_size(int prec) { return (prec == SG_F64 || prec == SG_DF64) ? 8 : (prec == SG_F32 ? 4 : 2); }
 
 extern "C" {
@@ -606,6 +626,27 @@ int sg_kl_coef(int n, int M, double sigma, double corr_len, const double* abar, 
   if (n < 3 || M < 0 || M > 64 || !coef_out || !(corr_len > 0) || !std::isfinite(sigma))
     return sg_fail(nullptr, SG_E_ARG, "sg_kl_coef: bad argument");
   return kl_coef_host(n, M, sigma, corr_len, abar, coef_out, lambda_out);
+}
+
+int sg_min_coef(int n, int M, const double* coef, double xi_max, double* amin_out) {
+  if (n < 3 || M < 0 || !coef || !amin_out || !(xi_max >= 0) || !std::isfinite(xi_max))
+    return sg_fail(nullptr, SG_E_ARG, "sg_min_coef: bad argument");
+  const size_t Nc = (size_t)(n - 1) * (n - 1);
+  double amin = INFINITY;
+  for (size_t e = 0; e < Nc; ++e) {
+    double s = 0;
+    for (int k = 1; k <= M; ++k) s += std::fabs(coef[(size_t)k * Nc + e]);
+    amin = std::min(amin, coef[e] - xi_max * s);
+  }
+  *amin_out = amin;
+  return SG_OK;
+}
+
+int sg_rhs(sg_handle h, const double* f_nodes, double* F) {
+  if (!h || !F) return h ? sg_fail(h, SG_E_ARG, "sg_rhs: null argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_rhs")) return rcd;
+  const double hh = 1.0 / (double)(h->n - 1);
+  return vec_load(h, f_nodes, hh * hh, F);
 }
 
 const char* sg_last_error(sg_handle h) {
@@ -633,6 +674,10 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
   h->nu1 = nu1, h->nu2 = nu2;
   h->omega = prob->omega > 0 ? prob->omega : 8.0 / 9.0;
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return sg_fail(nullptr, SG_E_CUDA, "sg_setup: no current CUDA device");
+  }
   build_basis(M, p, h->alpha, h->lvl_off);
   h->P = h->lvl_off.back();
   h->Np = (h->Nx * (size_t)h->P + 63) / 64 * 64;
@@ -716,6 +761,7 @@ int sg_basis(sg_handle h, int* alpha) {
 
 int sg_apply(sg_handle h, const void* X, void* Y, int prec) {
   if (!h || !X || !Y || prec < 0 || prec > 3) return h ? sg_fail(h, SG_E_ARG, "sg_apply: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_apply")) return rcd;
   const size_t lo = prec == SG_DF64 ? h->Nx * (size_t)h->P : 0;
   const int arith = (prec == SG_F64 || prec == SG_DF64) ? prec : SG_F32;
   return launch_apply(h, 0, prec, X, lo, prec, Y, lo, SG_F64, nullptr, 0, 0, h->P, 0, 0, arith);
@@ -723,33 +769,50 @@ int sg_apply(sg_handle h, const void* X, void* Y, int prec) {
 
 int sg_residual(sg_handle h, const double* F, const double* U, double* R) {
   if (!h || !F || !U || !R) return h ? sg_fail(h, SG_E_ARG, "sg_residual: null argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_residual")) return rcd;
   if ((const void*)U == (const void*)R) return sg_fail(h, SG_E_ARG, "sg_residual: U must not alias R");
   return apply_f64(h,0, SG_F64, U, SG_F64, R, F);
 }
 
 int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose) {
   if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocktri: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_precond_blocktri")) return rcd;
   return precond_blocktri(h, SG_F64, R, Z, prec, transpose != 0);
 }
 
 int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec) {
   if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blockdiag: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_precond_blockdiag")) return rcd;
   return precond_blockdiag(h, SG_F64, R, Z, prec);
 }
 
 int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec) {
   if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocksym: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_precond_blocksym")) return rcd;
   return precond_blocksym(h, SG_F64, R, Z, prec);
 }
 
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
   if (!h || !B || !X || prec < 0 || prec > 4 || prec == SG_DF64 || nblocks < 0 || nblocks > h->P)
     return h ? sg_fail(h, SG_E_ARG, "sg_vcycle: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_vcycle")) return rcd;
   return vcycle_run(h, prec, nblocks, B, SG_F64, X);
 }
 
+static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info_out);
+
+// Every return of sg_solve leaves info (when given) describing the call: an error that stops the call
+// before the solver has finished leaves it zeroed apart from its status.
 int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info_out) {
+  const int rc = solve_checked(h, F, U, opts, info_out);
+  if (info_out) info_out->status = rc;
+  return rc;
+}
+
+static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve_opts* opts, sg_solve_info* info_out) {
+  if (info_out) *info_out = sg_solve_info{};
   if (!h || !F || !U || !opts) return h ? sg_fail(h, SG_E_ARG, "sg_solve: null argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_solve")) return rcd;
   sg_solve_opts o = *opts;
   if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 3 || o.pc_prec < 0 || o.pc_prec > 4 ||
       o.pc_prec == SG_DF64 ||
@@ -757,9 +820,13 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
     return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
   if ((o.method == SG_GMRES || o.method == SG_FGMRES) && (o.restart < 1 || o.restart > 32))
     return sg_fail(h, SG_E_ARG, "sg_solve: restart must be 1..32");
-  if (o.arith != SG_ARITH_F64 && o.arith != SG_ARITH_DF64) return sg_fail(h, SG_E_ARG, "sg_solve: bad arith");
+  if (o.arith != SG_ARITH_F64 && o.arith != SG_ARITH_DF64 && o.arith != SG_ARITH_F64_DFOP)
+    return sg_fail(h, SG_E_ARG, "sg_solve: bad arith");
   if (o.arith == SG_ARITH_DF64 && (o.method != SG_FGMRES || o.pc_prec == SG_F64))
     return sg_fail(h, SG_E_ARG, "sg_solve: double-float mode needs FGMRES with an FP32 or BF16 preconditioner");
+  if (o.arith == SG_ARITH_F64_DFOP && ((o.method != SG_FGMRES && o.method != SG_GMRES) || o.pc_prec == SG_F64))
+    return sg_fail(h, SG_E_ARG, "sg_solve: the double-float operator mode needs (F)GMRES with an FP32 or BF16 "
+                                "preconditioner");
   sg_solve_info info{};
   const size_t N = h->Nx * (size_t)h->P;
   const bool dev = is_device_ptr(F) && is_device_ptr(U);
@@ -826,6 +893,7 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
 
 int sg_timing_enable(sg_handle h, int enable) {
   if (!h) return SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_timing_enable")) return rcd;
   SG_CUDA(h, cudaStreamSynchronize(h->stream));
   for (auto& s : h->tr.spans) h->tr.pool.push_back(s.a), h->tr.pool.push_back(s.b);
   h->tr.spans.clear();
@@ -836,6 +904,7 @@ int sg_timing_enable(sg_handle h, int enable) {
 
 int sg_timing_read(sg_handle h, double* ms, long long* launches) {
   if (!h) return SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_timing_read")) return rcd;
   SG_CUDA(h, cudaStreamSynchronize(h->stream));
   double acc[4] = {0, 0, 0, 0};
   for (auto& s : h->tr.spans) {
@@ -853,6 +922,7 @@ int sg_timing_read(sg_handle h, double* ms, long long* launches) {
 
 int sg_objective(sg_handle h, const double* U, double* J, double* G) {
   if (!h || !U || !J) return h ? sg_fail(h, SG_E_ARG, "sg_objective: null argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_objective")) return rcd;
   std::vector<double> mu(h->P);
   int rc = objective_dots(h, U, mu.data());
   if (rc) return rc;
@@ -868,6 +938,7 @@ int sg_objective(sg_handle h, const double* U, double* J, double* G) {
 
 int sg_adjoint_gradients(sg_handle h, const double* U, const double* Lam, double sigma, double* g_abar, double* g_sigma) {
   if (!h || !U || !Lam) return h ? sg_fail(h, SG_E_ARG, "sg_adjoint_gradients: null argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_adjoint_gradients")) return rcd;
   int rc;
   if (g_abar && (rc = adj_cell_forms(h, U, Lam, g_abar))) return rc;
   if (g_sigma) {

@@ -36,6 +36,9 @@ extern "C" int sg_solve_batch(sg_handle* hs, const double* const* F, double* con
   });
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SG_E_CUDA;
+  // every handle must belong to the current device (the worker threads run on it)
+  for (int s = 0; s < nsys; ++s)
+    if (const int rcd = sg_check_device(hs[s], "sg_solve_batch")) return rcd;
   const int nw = std::min(nstreams, nsys);
   std::vector<cudaStream_t> streams(nw, nullptr);
   for (int w = 0; w < nw; ++w)

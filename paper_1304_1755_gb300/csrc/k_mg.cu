@@ -471,6 +471,7 @@ size_t static_scratch_bytes(const sg_ctx* h, int nblocks, int prec) {
 extern "C" int sg_vcycle_static(sg_handle h, const double* B, void* X, int nblocks, int prec) {
   if (!h || !B || !X || prec < 0 || prec > 2 || nblocks < 0 || nblocks > h->P)
     return h ? sg_fail(h, SG_E_ARG, "sg_vcycle_static: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_vcycle_static")) return rcd;   // the array's address is per device
   if (nblocks == 0) return SG_OK;
   const size_t need = static_scratch_bytes(h, nblocks, prec);
   if (need > VCYCLE_SCRATCH_BYTES)

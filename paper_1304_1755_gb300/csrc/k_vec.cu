@@ -214,6 +214,12 @@ __global__ void k_fill(double* __restrict__ y, size_t N, double v) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) y[i] = v;
 }
 
+// F = e_0 (x) (w f): the mean PC block w f_s (w when f is null), every other block zero
+__global__ void k_load(const double* __restrict__ f, double w, double* __restrict__ F, size_t Nx, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    F[i] = i < Nx ? (f ? w * f[i] : w) : 0.0;
+}
+
 // split an FP64 vector into a double-float vector; positions [N, lo) of both halves are zeroed
 // (the padding of Krylov vectors must stay zero)
 __global__ void k_df_from_f64(const double* __restrict__ x, float* __restrict__ y, size_t N, size_t lo) {
@@ -465,6 +471,14 @@ int df_update(sg_ctx* h, float* U, size_t lo, int zprec, const void* Z, size_t l
 
 int vec_fill(sg_ctx* h, double* y, size_t N, double v) {
   k_fill<<<grid_for(N), 256, 0, h->stream>>>(y, N, v);
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  return SG_OK;
+}
+
+int vec_load(sg_ctx* h, const double* f, double w, double* F) {
+  const size_t N = h->Nx * (size_t)h->P;
+  k_load<<<grid_for(N), 256, 0, h->stream>>>(f, w, F, h->Nx, N);
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
   return SG_OK;

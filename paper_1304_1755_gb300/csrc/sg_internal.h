@@ -77,6 +77,7 @@ struct sg_ctx {
   int nu1 = 1, nu2 = 1;
   double omega = 8.0 / 9.0;
   bool const_mean = true;
+  int device = -1;                      // the CUDA device the handle was set up on
   cudaStream_t stream = nullptr;
   std::vector<int> alpha;               // P * M
   std::vector<int> lvl_off;             // p + 2 offsets of the degree levels
@@ -160,6 +161,8 @@ struct PhaseScope {
 
 // error helpers
 int sg_fail(sg_ctx* h, int code, const std::string& msg);
+// SG_OK when the calling thread's current device is the handle's, else SG_E_STATE (nothing launched)
+int sg_check_device(sg_ctx* h, const char* who);
 #define SG_CUDA(h, call)                                                          \
   do {                                                                            \
     cudaError_t e_ = (call);                                                      \
@@ -211,6 +214,8 @@ int vec_update(sg_ctx* h, double* U, int zprec, const void* Z, size_t ldz, int n
 int vec_cast(sg_ctx* h, int iprec, const void* in, int oprec, void* out, size_t N);
 int vec_axpby(sg_ctx* h, double a, const double* x, double b, double* y, size_t N);   // y = a x + b y
 int vec_fill(sg_ctx* h, double* y, size_t N, double v);    // by a kernel (also for mapped host memory)
+// F = e_0 (x) (w f): F[s] = w f[s] (w f when f is null) for s < Nx, zero for the other PC blocks
+int vec_load(sg_ctx* h, const double* f, double w, double* F);
 int vec_dot_pairs(sg_ctx* h, int npairs, const double* const* xs, const void* const* ys, const int* yprecs,
                   size_t N, double* out_host);
 int vec_axpy_prec(sg_ctx* h, double a, int xprec, const void* x, double* y, size_t N);  // y += a x

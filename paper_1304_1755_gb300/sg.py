@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsg.so")
 
 F64, F32, BF16, DF64, BF16Z = 0, 1, 2, 3, 4   # BF16Z: BF16 preconditioner storage, FP32 output
-ARITH_F64, ARITH_DF64 = 0, 1
+ARITH_F64, ARITH_DF64, ARITH_F64_DFOP = 0, 1, 2   # see sg_arith in include/sg.h
 LEGENDRE, HERMITE = 0, 1
 GMRES, FGMRES, GPCG, PCG, BGS = 0, 1, 2, 3, 4
 PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM = 0, 1, 2, 3
@@ -55,7 +55,9 @@ VP, DP, IP = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ct
 # exported name -> (restype, argtypes)
 SIGNATURES = {
     "sg_kl_coef": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, VP, VP, VP]),
+    "sg_min_coef": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, VP, ctypes.c_double, DP]),
     "sg_setup": (ctypes.c_int, [ctypes.POINTER(Problem), VP, ctypes.POINTER(VP)]),
+    "sg_rhs": (ctypes.c_int, [VP, VP, VP]),
     "sg_destroy": (None, [VP]),
     "sg_set_stream": (ctypes.c_int, [VP, VP]),
     "sg_last_error": (ctypes.c_char_p, [VP]),
@@ -120,6 +122,16 @@ def sg_kl_coef(n, M, sigma, corr_len=1.0, abar=None):
     return coef, lam[:M]
 
 
+def sg_min_coef(coef, n, M, xi_max=3.0 ** 0.5):
+    """Host coercivity check: min over cells and over the box |xi_k| <= xi_max of a(x_e, xi)."""
+    import numpy as np
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    assert c.shape == (M + 1, (n - 1) ** 2)
+    out = ctypes.c_double()
+    _check(lib().sg_min_coef(n, M, _ptr(c), xi_max, ctypes.byref(out)))
+    return out.value
+
+
 class Handle:
     """Owns one sg_handle.  Pointer arguments: torch tensors, numpy arrays or ints."""
 
@@ -157,6 +169,10 @@ class Handle:
         a = np.zeros((self.P, max(self.M, 1)), dtype=np.int32)
         _check(lib().sg_basis(self.h, _ptr(a)), self.h)
         return a[:, :self.M]
+
+    def rhs(self, F, f_nodes=None):
+        """sg_rhs: F = e_0 (x) h^2 f (device FP64; f_nodes device FP64 N_x values or None for f = 1)."""
+        _check(lib().sg_rhs(self.h, _ptr(f_nodes), _ptr(F)), self.h)
 
     def apply(self, X, Y, prec=F64):
         _check(lib().sg_apply(self.h, _ptr(X), _ptr(Y), prec), self.h)

@@ -18,6 +18,7 @@ def coefficients(n, M, sigma=0.3, mean="one", seed=7):
 
 class Pair:
     def __init__(self, n, M, p, family=basis.LEGENDRE, sigma=0.3, mean="one", nu=(1, 1), seed=7, coef=None):
+        self.memo = {}                      # oracle results a test module may reuse across parameters
         import torch
         from paper_1304_1755_gb300 import sg
         self.coef = coefficients(n, M, sigma, mean, seed) if coef is None else coef
@@ -53,3 +54,15 @@ def dev(x, dtype=None):
 def host(t):
     import torch
     return t.detach().to(torch.float64).cpu().numpy()
+
+
+_PAIRS = {}
+
+
+def pair(n, M, p, family=basis.LEGENDRE, sigma=0.3, mean="one", nu=(1, 1), seed=7):
+    """A Pair shared by the tests of one process (the oracle set-up of the large grids is the slow
+    part of these tests).  Users must not change the handle's state (stream, tuning)."""
+    key = (n, M, p, family, sigma, mean, tuple(nu), seed)
+    if key not in _PAIRS:
+        _PAIRS[key] = Pair(n, M, p, family, sigma=sigma, mean=mean, nu=nu, seed=seed)
+    return _PAIRS[key]

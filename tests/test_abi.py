@@ -77,6 +77,7 @@ def test_every_entry_point_rejects_a_null_handle_without_device(lib):
         lambda: lib.sg_adjoint_gradients(None, None, None, 0.1, None, ctypes.byref(D)),
         lambda: lib.sg_timing_enable(None, 1),
         lambda: lib.sg_timing_read(None, ms, ln),
+        lambda: lib.sg_rhs(None, None, None),
     ]
     for call in calls:
         assert call() == -1
@@ -106,3 +107,12 @@ def test_library_kl_helper_matches_oracle(lib, n, M, sigma):
     ab = np.linspace(0.5, 1.5, (n - 1) ** 2)
     coef2, _ = sg.sg_kl_coef(n, M, sigma, abar=ab)
     assert np.array_equal(coef2[0], ab)
+
+
+@pytest.mark.parametrize("n,M,sigma,xi", [(9, 2, 0.3, 3 ** 0.5), (33, 4, 0.5, 3 ** 0.5), (17, 6, 0.2, 2.5)])
+def test_library_coercivity_helper_matches_oracle(lib, n, M, sigma, xi):
+    """sg_min_coef (host) against the oracle's corner minimum, itself pinned by enumeration."""
+    from oracle import kl
+    from paper_1304_1755_gb300 import sg
+    coef = kl.kl_coefficients(n, M, sigma, abar=np.linspace(0.6, 1.4, (n - 1) ** 2))
+    assert sg.sg_min_coef(coef, n, M, xi) == pytest.approx(kl.min_coefficient_at_corners(coef, xi), abs=1e-15)

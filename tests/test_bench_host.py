@@ -30,4 +30,4 @@ def test_workload_sizes():
     c2 = bench.WORKLOADS["c2"]
     assert (c2["n"] - 2) ** 2 * math.comb(c2["M"] + c2["p"], c2["p"]) == 4_551_750
     # FP64 flop count of the canonical operator at C3: 67.2 per unknown
-    assert abs(bench.k1_flops(c3, False) / ((c3["n"] - 2) ** 2 * 210) - 67.2) < 1e-9
+    assert abs(bench.k1_method_flops(c3) / ((c3["n"] - 2) ** 2 * 210) - 67.2) < 1e-9

@@ -1,6 +1,8 @@
 """Parity at the full bandwidth-scale size (1025^2 grid, M = 6 Hermite, p = 4: 219,771,090
-unknowns), in the configuration the bench times (double-float FGMRES(20), BF16-storage
-preconditioner with FP32 output): the GPU solve must reach a true relative residual of 1e-8,
+unknowns), in the configuration the bench times (FGMRES(20) with an FP64 Arnoldi basis and
+Gram-Schmidt and the double-float outer operator, BF16-storage preconditioner with FP32
+output) and in the all-double-float Krylov variant: the library's load vector must equal the
+oracle's, the GPU solve must reach a true relative residual of 1e-8,
 and the FP64 residual the library computes must agree, at 4096 sampled (PC row, node) pairs,
 with the oracle's own evaluation of F - A U at those pairs (Eq. tensor-product, written out
 per node from the Q1 element matrix and the closed-form G_k).  The oracle cannot solve or even
@@ -45,7 +47,8 @@ def _sampled_residual(coef, Gs, U, F, rows, nodes, n):
     return r, scale
 
 
-def test_c3_fullsize_residual_at_sampled_outputs():
+@pytest.mark.parametrize("arith", [sg.ARITH_F64_DFOP, sg.ARITH_DF64], ids=["f64_dfop", "df64"])
+def test_c3_fullsize_residual_at_sampled_outputs(arith):
     import torch
     n, M, p = N_, M_, P_DEG
     coef = kl.kl_coefficients(n, M, SIG)
@@ -53,11 +56,14 @@ def test_c3_fullsize_residual_at_sampled_outputs():
     Gs = basis.g_matrices(alphas, basis.HERMITE)          # G_0 = I, G_1 .. G_M
     h = sg.Handle(n, M, p, sg.HERMITE, coef, stream=torch.cuda.current_stream())
     N = h.P * h.Nx
-    F = torch.zeros(N, dtype=torch.float64, device="cuda")
-    F[:h.Nx] = 1.0 / (n - 1) ** 2
+    F = torch.empty(N, dtype=torch.float64, device="cuda")
+    h.rhs(F)
+    torch.cuda.synchronize()
+    F0 = F[:h.Nx].cpu().numpy()
+    assert np.array_equal(F0, fem.load_vector(n)) and float(F[h.Nx:].abs().max()) == 0.0
     U = torch.zeros_like(F)
     info = h.solve(F, U, method=sg.FGMRES, precond=sg.PC_BLOCKTRI, restart=20, maxit=200, tol=1e-8,
-                   pc_prec=sg.BF16Z, arith=sg.ARITH_DF64)
+                   pc_prec=sg.BF16Z, arith=arith)
     assert info.status == 0 and info.relres_true <= 1e-8
     R = torch.empty_like(F)
     h.residual(F, U, R)

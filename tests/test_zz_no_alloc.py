@@ -1,11 +1,13 @@
-"""sg_vcycle_static, the allocation-free V-cycle, against sg_vcycle on the same inputs.
+"""sg_vcycle_static, the allocation-free V-cycle, against sg_vcycle and against the oracle.
 
-Both entry points launch the same level kernels, so the results agree to rounding (the
-test allows 1e-13 relative for FP64 and the storage precision's unit roundoff
-otherwise).  Two calls in a row with different right-hand sides check that the shared
-array's leftover contents from the previous call do not leak into the next one, and the
-device's free memory is unchanged across the second call (the first call on a device may
-load the library's device code, which the runtime allocates itself)."""
+Both entry points launch the same level kernels with the same arithmetic; only where the coarse
+levels live differs (the handle's workspace or the library's static array), so the results
+must be bit-identical.  They must also match the oracle's V-cycle within the storage
+precision's tolerance (the bar of the V-cycle parity tests).  Two calls in a row with different
+right-hand sides check that the shared array's leftover contents from the previous call do not
+leak into the next one, and the device's free memory is unchanged across the second call (the
+first call on a device may load the library's device code, which the runtime allocates
+itself).  At 513^2 the tile kernels run with several tiles per level row."""
 import ctypes
 
 import numpy as np
@@ -16,7 +18,13 @@ from _gpu_util import Pair, dev, host
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 1e-6, 2: 1e-2}
+def _oracle_ok(got, ref, prec):
+    """The V-cycle parity bar: FP64 1e-11 and FP32 1e-4 of max |ref| elementwise, BF16 3e-2 in norm."""
+    if prec == 0:
+        return np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    if prec == 1:
+        return np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    return np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref)
 
 
 def _call(fn, pr, B, X, nb, prec):
@@ -33,14 +41,14 @@ def _out(pr, nb, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2], ids=["f64", "f32", "bf16"])
-@pytest.mark.parametrize("n", [129, 33], ids=["n129", "n33"])
-def test_static_vcycle_matches_vcycle_on_two_calls(n, prec):
+@pytest.mark.parametrize("n,nb", [(129, 6), (33, 6), (513, 4)], ids=["n129", "n33", "n513"])
+def test_static_vcycle_matches_vcycle_on_two_calls(n, nb, prec):
     import torch
     L = sg.lib()
-    pr = Pair(n, 2, 2)                                 # P = 6 blocks
-    nb = pr.sys.P
-    B1 = dev(inputs.uniform(41, nb * pr.sys.Nx))
-    B2 = dev(inputs.uniform(42, nb * pr.sys.Nx) * 1e3)
+    pr = Pair(n, 2, 2)                                 # P = 6 blocks of workspace
+    B1h = inputs.uniform(41, (nb, pr.sys.Nx))
+    B2h = inputs.uniform(42, (nb, pr.sys.Nx)) * 1e3
+    B1, B2 = dev(B1h.reshape(-1)), dev(B2h.reshape(-1))
     X1, X2, R1, R2 = (_out(pr, nb, prec) for _ in range(4))
     _call(L.sg_vcycle_static, pr, B1, X1, nb, prec)
     free_before = torch.cuda.mem_get_info()[0]
@@ -48,10 +56,11 @@ def test_static_vcycle_matches_vcycle_on_two_calls(n, prec):
     assert torch.cuda.mem_get_info()[0] == free_before
     _call(L.sg_vcycle, pr, B1, R1, nb, prec)
     _call(L.sg_vcycle, pr, B2, R2, nb, prec)
-    got1, got2, ref1, ref2 = (host(t) for t in (X1, X2, R1, R2))
-    for got, ref in ((got1, ref1), (got2, ref2)):
+    assert torch.equal(X1, R1) and torch.equal(X2, R2)
+    for X, Bh in ((X1, B1h), (X2, B2h)):
+        got = host(X).reshape(nb, -1)
         assert np.isfinite(got).all()
-        assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max()
+        assert _oracle_ok(got, pr.hier.vcycle(Bh.T).T, prec)
 
 
 def test_static_vcycle_rejects_oversize_request():
