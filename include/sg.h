@@ -78,8 +78,19 @@ typedef enum { SG_LEGENDRE = 0, SG_HERMITE = 1 } sg_family;
 /* SG_BGS: the stationary block Gauss-Seidel iteration U += B_T^{-1}(F - A U) (Sec. 4.2). */
 typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3, SG_BGS = 4 } sg_method;
 /* SG_PC_BLOCKSYM: B_S = B_T diag(A)^{-1} B_T^T, the symmetric block Gauss-Seidel
- * preconditioner of Sec. 4.2 (lower sweep, the exact diagonal blocks K_0, upper sweep). */
-typedef enum { SG_PC_NONE = 0, SG_PC_BLOCKTRI = 1, SG_PC_BLOCKDIAG = 2, SG_PC_BLOCKSYM = 3 } sg_pc;
+ * preconditioner of Sec. 4.2 (lower sweep, the exact diagonal blocks K_0, upper sweep).
+ * SG_PC_BLOCKTRI_EXACT: the 2 x 2 block-triangular form of Sec. 4.2 / Theorem 1,
+ * B = [A_hat 0; W D] with A_hat the Galerkin matrix of total degree p-1 solved by an inner
+ * FGMRES (right-preconditioned by the flat B_T of A_hat, to inner_tol) and the degree-p
+ * diagonal blocks D = I (x) K_0 by one V-cycle each (see sg_precond_blocktri_exact).
+ * With FGMRES and pc_prec = SG_F64 only; an analysis form, each application costs a solve. */
+typedef enum {
+  SG_PC_NONE = 0,
+  SG_PC_BLOCKTRI = 1,
+  SG_PC_BLOCKDIAG = 2,
+  SG_PC_BLOCKSYM = 3,
+  SG_PC_BLOCKTRI_EXACT = 4
+} sg_pc;
 
 /* One SG problem (Sec. 2-3).  coef is a HOST array of (M+1) rows of (n-1)^2
  * per-cell values, cell e = cx + cy (n-1): row 0 is the mean coefficient
@@ -113,7 +124,9 @@ typedef struct {
  * adjoint solve; B_T^T is the upper block-triangular sweep).  x0_given: U holds
  * an initial guess (else U = 0 is used).  reorth: 0 classical Gram-Schmidt,
  * 1 classical Gram-Schmidt with a second pass when the norm drops by more than
- * 1/sqrt(2) (selective reorthogonalisation).  arith: sg_arith. */
+ * 1/sqrt(2) (selective reorthogonalisation).  arith: sg_arith.  inner_tol, inner_restart:
+ * tolerance (0 selects 1e-12) and restart (0 selects 30) of the inner solves of
+ * SG_PC_BLOCKTRI_EXACT; ignored by the other preconditioners. */
 typedef struct {
   int method;
   int precond;
@@ -125,6 +138,8 @@ typedef struct {
   int x0_given;
   int reorth;
   int arith;
+  double inner_tol;
+  int inner_restart;
 } sg_solve_opts;
 
 /* Filled by sg_solve. iters = preconditioner applications (Arnoldi steps);
@@ -196,6 +211,18 @@ int sg_residual(sg_handle h, const double* F, const double* U, double* R);
 int sg_precond_blocktri(sg_handle h, const double* R, void* Z, int prec, int transpose);
 /* Z = B_D^{-1} R (Sec. 4.1): one V-cycle on every PC block. */
 int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec);
+/* Z = B^{-1} R for the 2 x 2 block-triangular preconditioner of Sec. 4.2 whose lower-degree block
+ * is the exact A_hat (Theorem 1's form; Eq. hierarchical_structure splits A_p into A_hat = A_{p-1},
+ * the coupling W and the degree-p diagonal D = I (x) K_0):
+ *   Z_low = A_hat^{-1} R_low,  Z_p = D^{-1}(R_p - W Z_low)           (transpose = 0)
+ *   Z_p = D^{-T} R_p,          Z_low = A_hat^{-T}(R_low - W^T Z_p)  (transpose != 0).
+ * A_hat^{-1} is an inner FGMRES(30) solve to a relative residual of inner_tol (0 selects 1e-12),
+ * right-preconditioned by the flat B_T of A_hat in FP64, on a degree-(p-1) handle the first call
+ * creates and the handle keeps; D^{-1} is one FP64 V-cycle per block.  R, Z: device FP64,
+ * P * N_x values (Z must not alias R).  For p = 0 (no lower block) this is one V-cycle.
+ * Synchronises the handle's stream (the inner solves do); returns the inner solve's status
+ * (SG_E_NOCONV when it reached its iteration limit, Z then holds its last iterate). */
+int sg_precond_blocktri_exact(sg_handle h, const double* R, double* Z, int transpose, double inner_tol);
 /* Z = B_S^{-1} R (Sec. 4.2): lower sweep, multiplication by the diagonal blocks K_0
  * (exact), upper sweep; symmetric positive definite, for PCG.  R FP64, Z in prec. */
 int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec);

@@ -152,7 +152,14 @@ double host_dot(sg_ctx* h, const double* x, const double* y, size_t N, int* rc) 
   return out;
 }
 
+int precond_blocktri_exact(sg_ctx* h, const double* R, double* Z, int transpose);
+
 int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec, int transpose) {
+  if (pc == SG_PC_BLOCKTRI_EXACT) {
+    if (rprec != SG_F64 || prec != SG_F64) return sg_fail(h, SG_E_ARG, "exact block-triangular preconditioner: FP64 only");
+    const int rc = precond_blocktri_exact(h, (const double*)R, (double*)Z, transpose);
+    return rc == SG_E_NOCONV ? SG_OK : rc;       // an inner solve at its limit still gives a usable Z
+  }
   if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, rprec, R, Z, prec, transpose);
   if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, rprec, R, Z, prec);
   if (pc == SG_PC_BLOCKSYM) return precond_blocksym(h, rprec, R, Z, prec);
@@ -189,6 +196,8 @@ int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec, int layout = -1) {
     h->kz_cap = std::max(nz, 1);
     h->kz_prec = zprec;
   }
+  if (!h->qmax && cudaMalloc(&h->qmax, sizeof(unsigned) * (SG_MAX_RESTART + 1) * (size_t)h->P) != cudaSuccess)
+    return sg_fail(h, SG_E_ALLOC, "alloc grid maxima");
   if (!h->ktmp) {
     if (cudaMalloc(&h->ktmp, sizeof(double) * Np * 4) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc work vectors");
     SG_CUDA(h, cudaMemsetAsync(h->ktmp, 0, sizeof(double) * Np * 4, h->stream));
@@ -230,11 +239,23 @@ struct OpsF64 {
     return apply_f64(h, 0, SG_F64, U, SG_F64, v(0), F);
   }
   int norm2(int l, double* out) { int rc; *out = host_dot(h, v(l), v(l), N, &rc); return rc; }
-  int precond(int j) { return apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose); }
+  // FP32 z_j are read through their blocks' fixed-point grids (SG_F32Q) by the operator and by the
+  // solution update alike, so the flexible basis is the grid values z'_j (the flexible method takes
+  // whatever z_j it is given); the double-float operator then forms cell features by exact FP32
+  // differences instead of error-free sums.  The block maxima of z_j are kept for the update.
+  bool quant() const { return dfop && flexible && zprec_of(o.pc_prec) == SG_F32; }
+  unsigned* qm(int j) const { return h->qmax + (size_t)j * h->P; }
+  int precond(int j) {
+    int rc = apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose);
+    if (rc || !quant()) return rc;
+    return block_absmax(h, (const float*)z(j), qm(j));
+  }
   int apply(int j) {
-    if (dfop)    // FP32-class z_j is exact in double-float; w is rounded once to FP64 on the store
-      return launch_apply(h, 0, zprec_of(o.pc_prec), z(j), 0, SG_F64, v(j + 1), 0, SG_F64, nullptr, 0, 0, h->P, 0, 0,
-                          SG_DF64);
+    if (dfop) {  // FP32-class z_j is exact in double-float; w is rounded once to FP64 on the store
+      h->qcur = quant() ? qm(j) : nullptr;
+      return launch_apply(h, 0, quant() ? SG_F32Q : zprec_of(o.pc_prec), z(j), 0, SG_F64, v(j + 1), 0, SG_F64,
+                          nullptr, 0, 0, h->P, 0, 0, SG_DF64);
+    }
     return apply_f64(h, 0, zprec_of(o.pc_prec), z(j), SG_F64, v(j + 1), nullptr);
   }
   int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
@@ -242,6 +263,7 @@ struct OpsF64 {
   int update(int k, const double* y) {
     int rc0 = spec_invalidate(h);
     if (rc0) return rc0;
+    if (quant()) return vec_update_q(h, U, (const float*)h->kz, h->Np, k, y, N, h->qmax);
     if (flexible) return vec_update(h, U, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N);
     double* t = h->ktmp;
     SG_CUDA(h, cudaMemsetAsync(t, 0, sizeof(double) * N, h->stream));
@@ -304,14 +326,24 @@ struct OpsDF {
     if ((rc = df_dots(h, nullptr, 0, 0, v(l), h->Np, true))) return rc;
     return copy_red(h, 0, 1, out);
   }
-  int precond(int j) { return apply_precond(h, o.precond, SG_F32, v(j), z(j), o.pc_prec, o.transpose); }
+  bool quant() const { return zprec_of(o.pc_prec) == SG_F32; }     // grid-read z_j, as in OpsF64
+  unsigned* qm(int j) const { return h->qmax + (size_t)j * h->P; }
+  int precond(int j) {
+    int rc = apply_precond(h, o.precond, SG_F32, v(j), z(j), o.pc_prec, o.transpose);
+    if (rc || !quant()) return rc;
+    return block_absmax(h, (const float*)z(j), qm(j));
+  }
   int apply(int j) {
-    return launch_apply(h, 0, zprec_of(o.pc_prec), z(j), 0, SG_DF64, v(j + 1), h->Np, SG_DF64, nullptr, 0, 0, h->P, 0, 0,
-                        SG_DF64);
+    h->qcur = quant() ? qm(j) : nullptr;
+    return launch_apply(h, 0, quant() ? SG_F32Q : zprec_of(o.pc_prec), z(j), 0, SG_DF64, v(j + 1), h->Np, SG_DF64,
+                        nullptr, 0, 0, h->P, 0, 0, SG_DF64);
   }
   int dots(int j, bool ww) { return df_dots(h, V, 2 * h->Np, j + 1, v(j + 1), h->Np, ww); }
   int axpys(int j, const double* c) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, c, v(j + 1), h->Np); }
-  int update(int k, const double* y) { return df_update(h, Ud, h->Np, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N); }
+  int update(int k, const double* y) {
+    if (quant()) return df_update_q(h, Ud, h->Np, (const float*)h->kz, h->Np, k, y, N, h->qmax);
+    return df_update(h, Ud, h->Np, zprec_of(o.pc_prec), h->kz, h->Np, k, y, N);
+  }
   int finish() {
     if (h->true_res_valid) return SG_OK;       // the converged check already wrote this iterate to U
     int rc = spec_invalidate(h);
@@ -579,11 +611,65 @@ int solve_pcg(sg_ctx* h, const double* F, double* U, const sg_solve_opts& o, sg_
   return SG_OK;
 }
 
+// The 2 x 2 block-triangular preconditioner with the exact lower-degree block (Sec. 4.2, Theorem 1).
+// The PC basis is degree-graded, so the first lvl_off[p] blocks of an SG vector are a vector of the
+// degree-(p-1) system A_hat = A_{p-1}, solved on a child handle of that degree.
+int precond_blocktri_exact(sg_ctx* h, const double* R, double* Z, int transpose) {
+  int rc;
+  if (h->p == 0) return precond_blocktri(h, SG_F64, R, Z, SG_F64, transpose);
+  if (!h->child) {
+    sg_problem pr{h->n, h->M, h->p - 1, h->family, h->coef_h.data(), h->nu1, h->nu2, h->omega};
+    sg_handle c = nullptr;
+    if ((rc = sg_setup(&pr, h->stream, &c))) return sg_fail(h, rc, "exact block-triangular: set-up of the degree p-1 "
+                                                                     "system failed: " + std::string(sg_last_error(nullptr)));
+    h->child = c;
+  }
+  sg_ctx* c = h->child;
+  c->stream = h->stream;
+  if ((rc = ensure_prec_work(h, SG_F64))) return rc;
+  const int nlow = h->lvl_off[h->p], np = h->P - nlow;
+  const size_t Nx = h->Nx;
+  sg_solve_opts io{};
+  io.method = SG_FGMRES, io.precond = SG_PC_BLOCKTRI, io.restart = h->inner_restart, io.maxit = 2000;
+  io.tol = h->inner_tol, io.pc_prec = SG_F64, io.transpose = transpose, io.arith = SG_ARITH_F64;
+  sg_solve_info info{};
+  const long long before = c->tr.launches[0] + c->tr.launches[1] + c->tr.launches[2] + c->tr.launches[3];
+  int rin;
+  if (!transpose) {
+    rin = sg_solve(c, R, Z, &io, &info);                                          // Z_low = A_hat^{-1} R_low
+    if (rin != SG_OK && rin != SG_E_NOCONV) return sg_fail(h, rin, std::string("exact block-triangular: ") + c->err);
+    double* T = (double*)h->work[SG_F64].T;                                       // T = R_p - W Z_low
+    if ((rc = launch_apply(h, 1, SG_F64, Z, 0, SG_F64, T, 0, SG_F64, R, 0, nlow, np, nlow, 0, SG_F64))) return rc;
+    if ((rc = vcycle_run(h, SG_F64, np, T, SG_F64, Z + (size_t)nlow * Nx, true))) return rc;
+  } else {
+    if ((rc = vcycle_run(h, SG_F64, np, R + (size_t)nlow * Nx, SG_F64, Z + (size_t)nlow * Nx, false))) return rc;
+    if (!h->xbuf && cudaMalloc(&h->xbuf, sizeof(double) * Nx * h->P) != cudaSuccess)
+      return sg_fail(h, SG_E_ALLOC, "alloc exact block-triangular buffer");
+    // T_low = R_low - W^T Z_p: only the degree p-1 rows couple to degree p
+    const int r1 = h->lvl_off[h->p - 1], n1 = nlow - r1;
+    SG_CUDA(h, cudaMemcpyAsync(h->xbuf, R, sizeof(double) * Nx * r1, cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = launch_apply(h, 2, SG_F64, Z, 0, SG_F64, h->xbuf + (size_t)r1 * Nx, 0, SG_F64, R, 0, r1, n1, r1, 0,
+                           SG_F64)))
+      return rc;
+    rin = sg_solve(c, h->xbuf, Z, &io, &info);                                    // Z_low = A_hat^{-T} T_low
+    if (rin != SG_OK && rin != SG_E_NOCONV) return sg_fail(h, rin, std::string("exact block-triangular: ") + c->err);
+  }
+  const long long after = c->tr.launches[0] + c->tr.launches[1] + c->tr.launches[2] + c->tr.launches[3];
+  count_launch(h, (int)(after - before));
+  return rin;
+}
+
 void destroy_ctx(sg_ctx* h) {
   if (!h) return;
+  if (h->child) {
+    destroy_ctx(h->child);
+    h->child = nullptr;
+  }
+  cudaFree(h->xbuf);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
   cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->w64), cudaFree(h->pvec);
+  cudaFree(h->qmax);
   free_terms(h->t_all), free_terms(h->t_lower), free_terms(h->t_upper), free_terms(h->t_off), free_terms(h->t_diag);
   for (int l = 0; l < SG_MAX_LEVELS; ++l) cudaFree(h->lev[l].st64), cudaFree(h->lev[l].st32);
   for (auto& W : h->work) {
@@ -618,7 +704,9 @@ int sg_check_device(sg_ctx* h, const char* who) {
   return SG_OK;
 }
 
-size_t prec_size(int prec) { return (prec == SG_F64 || prec == SG_DF64) ? 8 : (prec == SG_F32 ? 4 : 2); }
+size_t prec_size(int prec) {
+  return (prec == SG_F64 || prec == SG_DF64) ? 8 : ((prec == SG_F32 || prec == SG_F32Q) ? 4 : 2);
+}
 
 extern "C" {
 
@@ -786,6 +874,15 @@ int sg_precond_blockdiag(sg_handle h, const double* R, void* Z, int prec) {
   return precond_blockdiag(h, SG_F64, R, Z, prec);
 }
 
+int sg_precond_blocktri_exact(sg_handle h, const double* R, double* Z, int transpose, double inner_tol) {
+  if (!h || !R || !Z || (const void*)R == (const void*)Z || !(inner_tol >= 0))
+    return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocktri_exact: bad argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_precond_blocktri_exact")) return rcd;
+  h->inner_tol = inner_tol > 0 ? inner_tol : 1e-12;
+  h->inner_restart = 30;
+  return precond_blocktri_exact(h, R, Z, transpose != 0);
+}
+
 int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec) {
   if (!h || !R || !Z || prec < 0 || prec > 4 || prec == SG_DF64) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocksym: bad argument") : SG_E_ARG;
   if (const int rcd = sg_check_device(h, "sg_precond_blocksym")) return rcd;
@@ -814,7 +911,7 @@ static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve
   if (!h || !F || !U || !opts) return h ? sg_fail(h, SG_E_ARG, "sg_solve: null argument") : SG_E_ARG;
   if (const int rcd = sg_check_device(h, "sg_solve")) return rcd;
   sg_solve_opts o = *opts;
-  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 3 || o.pc_prec < 0 || o.pc_prec > 4 ||
+  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 4 || o.pc_prec < 0 || o.pc_prec > 4 ||
       o.pc_prec == SG_DF64 ||
       !(o.tol > 0) || o.maxit < 0)
     return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
@@ -822,6 +919,13 @@ static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve
     return sg_fail(h, SG_E_ARG, "sg_solve: restart must be 1..32");
   if (o.arith != SG_ARITH_F64 && o.arith != SG_ARITH_DF64 && o.arith != SG_ARITH_F64_DFOP)
     return sg_fail(h, SG_E_ARG, "sg_solve: bad arith");
+  if (o.precond == SG_PC_BLOCKTRI_EXACT &&
+      (o.method != SG_FGMRES || o.pc_prec != SG_F64 || o.arith != SG_ARITH_F64 || !(o.inner_tol >= 0) ||
+       o.inner_restart < 0 || o.inner_restart > 32))
+    return sg_fail(h, SG_E_ARG, "sg_solve: the exact block-triangular preconditioner needs FGMRES in FP64 "
+                                "(pc_prec SG_F64, arith SG_ARITH_F64) and inner_restart <= 32");
+  h->inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-12;
+  h->inner_restart = o.inner_restart > 0 ? o.inner_restart : 30;
   if (o.arith == SG_ARITH_DF64 && (o.method != SG_FGMRES || o.pc_prec == SG_F64))
     return sg_fail(h, SG_E_ARG, "sg_solve: double-float mode needs FGMRES with an FP32 or BF16 preconditioner");
   if (o.arith == SG_ARITH_F64_DFOP && ((o.method != SG_FGMRES && o.method != SG_GMRES) || o.pc_prec == SG_F64))

@@ -48,6 +48,7 @@ struct ApplyArgs {
   const df2* wdf;      // optional table of weights c_k(e) gamma_n as double-float, slot-major
   const double* w64;   // optional table of the same weights in FP64
   const int* ws;       // weight slot of each term
+  const unsigned* qmax; // SG_F32Q input: block maxima of X (its grid scales)
   const int* row_ptr;
   const int* tj;
   const int* tk;
@@ -81,6 +82,20 @@ template <> struct Load<bf16> {
   typedef bf16 E;
   static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return ok ? __bfloat162float(__ldg(p)) : 0.f; }
   static __device__ __forceinline__ Z zero() { return 0.f; }
+};
+// FP32 storage read through per-block fixed-point grids (SG_F32Q): the kernel turns each loaded value
+// into the biased integer fma(z, s_j, 1.5 2^23) of its grid value and scales the coupling's weight by
+// the block's quantum, so the double-float policy forms its cell features by plain FP32 differences,
+// which are exact for such values
+struct QF32 {};
+struct qf {
+  float v;
+};
+template <> struct Load<QF32> {
+  typedef qf Z;
+  typedef float E;
+  static __device__ __forceinline__ Z ldq(const E* p, size_t, bool ok) { return qf{ok ? __ldg(p) : 0.f}; }
+  static __device__ __forceinline__ Z zero() { return qf{0.f}; }
 };
 template <> struct Load<DFS> {
   typedef df2 Z;
@@ -219,6 +234,17 @@ struct ArDF {
     dacc_fma(s.d2, w, f2);
     dacc_fma(s.hg, w, f3);
   }
+  // biased grid integers (SG_F32Q): 1.5 2^23 + k with |k| < 2^22, so the two differences
+  // (< 2^23) and the alternating sum (< 2^24) are integers that FP32 holds exactly, and so are
+  // their products with the block's quantum q (a power of two, at least 2^-107): the exact features
+  static __device__ __forceinline__ void qterm(State& s, T w, float za, float zb, float zc, float zd, float q) {
+    const float f1 = __fmul_rn(__fsub_rn(za, zc), q);
+    const float f2 = __fmul_rn(__fsub_rn(zb, zd), q);
+    const float f3 = __fmul_rn(__fadd_rn(__fsub_rn(za, zb), __fsub_rn(zc, zd)), q);
+    dacc_fma(s.d1, w, f1);
+    dacc_fma(s.d2, w, f2);
+    dacc_fma(s.hg, w, f3);
+  }
   static __device__ __forceinline__ df2 dsub(df2 a, df2 b) {
     float s, e;
     two_sum(a.hi, -b.hi, s, e);
@@ -332,6 +358,7 @@ template <class AR, typename XE> struct RowTerms {
   const XE* xp[MAXT];
   const typename AR::CE* wp[MAXT];
   typename AR::G g[MAXT];
+  float qs[MAXT], qq[MAXT];        // SG_F32Q: grid scale and quantum of the coupled column's block
 };
 
 template <class AR, bool WT, typename TXS, typename TYS, typename TRS>
@@ -352,6 +379,10 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
     rt.xp[t] = (const XE*)a.X + (size_t)a.tj[t0 + t] * a.Nx;
     rt.wp[t] = AR::template cbase<WT>(a) + (size_t)(WT ? a.ws[t0 + t] : a.tk[t0 + t]) * a.Nc;
     rt.g[t] = AR::gval(a, t0 + t);
+    if constexpr (std::is_same<TXS, QF32>::value) {
+      const unsigned mb = a.qmax[a.tj[t0 + t]];
+      rt.qs[t] = qgrid_scale(mb), rt.qq[t] = qgrid_quantum(mb);
+    }
   }
   __syncthreads();
   const int gw = blockIdx.y * WARPS + (threadIdx.x >> 5);
@@ -385,7 +416,13 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
       const Z zb = LX::ldq(p + 1, xlo, okb);
       const Z zc = LX::ldq(p + 1 + m, xlo, okc);
       const Z zd = LX::ldq(p + m, xlo, okd);
-      AR::term(st, w, za, zb, zc, zd);
+      if constexpr (std::is_same<TXS, QF32>::value) {
+        const float sq = rt.qs[t];                         // exact: the product is rounded once, to an integer
+        AR::qterm(st, w, __fmaf_rn(za.v, sq, SG_QBIAS), __fmaf_rn(zb.v, sq, SG_QBIAS), __fmaf_rn(zc.v, sq, SG_QBIAS),
+                  __fmaf_rn(zd.v, sq, SG_QBIAS), rt.qq[t]);
+      } else {
+        AR::term(st, w, za, zb, zc, zd);
+      }
     }
     T Ac, Bc, Cc;
     AR::features(st, Ac, Bc, Cc);
@@ -413,8 +450,116 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
   }
 }
 
+// FP32 arithmetic, two cells per lane.  Lane l of a warp owns the cells cx0 = X + 2l and cx0 + 1
+// of each cell row (X = 62 w, even, so the cells' coefficient pair is one aligned 8-byte load;
+// consecutive warps overlap by two cells) and walks a strip of cell rows
+// for one output row i.  Per cell row and coupling it loads its two node columns in the two node rows
+// of the cell row (the third column, cx0 + 2, comes from the right lane by a shuffle; lane 31 loads
+// it), loads the two cells' coefficients as one 8-byte pair (the cell rows have an even length) and
+// mixes the corners with four multiply-adds per cell.  It finishes node cx0 + 1 from its own two
+// cells in this and the previous cell row, and node cx0 from its first cell and the left lane's
+// second cell, whose contribution arrives in one shuffle.  Lane 0 only supplies its cells (node
+// X + 1 is the previous warp's lane 31's), except in the first warp, whose lane 0 finishes node 1;
+// so warp w writes nodes 62 w + 2 .. 62 w + 63 once each.  About half
+// the load and address instructions per coupling of the one-cell-per-lane kernel, which leaves this
+// bandwidth-bound form issue-bound.
+template <typename TXS, typename TYS, typename TRS>
+__global__ void __launch_bounds__(NT) k_apply_f32x2(ApplyArgs a) {
+  typedef ArF32 AR;
+  typedef Load<TXS> LX;
+  typedef typename LX::E XE;
+  typedef Epi<AR, TRS> E;
+  __shared__ const XE* xp[MAXT];
+  __shared__ const float* wp[MAXT];
+  __shared__ float gg[MAXT];
+  const int i = a.row0 + blockIdx.x;
+  const int t0 = a.row_ptr[i];
+  const int nt = a.row_ptr[i + 1] - t0;
+  for (int t = threadIdx.x; t < nt; t += NT) {
+    xp[t] = (const XE*)a.X + (size_t)a.tj[t0 + t] * a.Nx;
+    wp[t] = a.c32 + (size_t)a.tk[t0 + t] * a.Nc;
+    gg[t] = a.g32[t0 + t];
+  }
+  __syncthreads();
+  const int gw = blockIdx.y * WARPS + (threadIdx.x >> 5);
+  if (gw >= a.nwx * a.nstrips) return;
+  const int lane = threadIdx.x & 31;
+  const int n = a.n, m = a.m;
+  const int wx = gw % a.nwx;
+  const int cx0 = 62 * wx + 2 * lane;                       // first cell (= vertex column of its SW corner)
+  const int cy0 = a.strip * (gw / a.nwx);
+  const int cy1 = min(cy0 + a.strip, n - 2);
+  // columns cx0, cx0 + 1, cx0 + 2 interior?
+  const bool ok0 = cx0 >= 1 && cx0 <= n - 2, ok1 = cx0 + 1 <= n - 2, ok2 = cx0 + 2 <= n - 2;
+  const bool cellA = cx0 <= n - 2, cellB = cx0 + 1 <= n - 2;   // cells inside the grid of cells
+  const bool outA = lane >= 1 && ok0, outB = ok1 && (lane >= 1 || wx == 0);   // nodes cx0, cx0 + 1 finished here
+  const int cxw = min(cx0, n - 3);                             // weight pair (cells n - 3, n - 2 at most; n - 3 is even)
+  const bool wshift = cxw != cx0;                              // only past the last cell pair (weights unused)
+  float AAp = 0.f, BAp = 0.f, CAp = 0.f, ABp = 0.f, BBp = 0.f, CBp = 0.f;   // previous cell row's features
+  typename E::Raw rvA{}, rvB{};
+  for (int cy = cy0; cy <= cy1; ++cy) {
+    const bool out_row = cy > cy0;
+    const int sA = (cx0 - 1) + (cy - 1) * m;                   // interior index of vertex (cx0, cy)
+    if (out_row) {
+      if (outA) rvA = E::ld(a.R, a.rlo, (size_t)(i - a.rbase) * a.Nx + sA);
+      if (outB) rvB = E::ld(a.R, a.rlo, (size_t)(i - a.rbase) * a.Nx + sA + 1);
+    }
+    const bool lo_ok = cy >= 1, hi_ok = cy + 1 <= n - 2;
+    const int e = cxw + cy * (n - 1);
+    float a0 = 0.f, b0 = 0.f, c0 = 0.f, d0 = 0.f;              // cell A corners mixed
+    float a1 = 0.f, b1 = 0.f, c1 = 0.f, d1 = 0.f;              // cell B
+#pragma unroll 4
+    for (int t = 0; t < nt; ++t) {
+      const XE* p = xp[t] + sA;
+      const float2 cw = __ldg(reinterpret_cast<const float2*>(wp[t] + e));
+      const float g = gg[t];
+      const float wA = (wshift ? cw.y : cw.x) * g, wB = cw.y * g;
+      const float z0b = LX::ldq(p, 0, ok0 && lo_ok), z1b = LX::ldq(p + 1, 0, ok1 && lo_ok);
+      const float z0t = LX::ldq(p + m, 0, ok0 && hi_ok), z1t = LX::ldq(p + m + 1, 0, ok1 && hi_ok);
+      float z2b = __shfl_down_sync(0xffffffffu, z0b, 1), z2t = __shfl_down_sync(0xffffffffu, z0t, 1);
+      if (lane == 31) {
+        z2b = LX::ldq(p + 2, 0, ok2 && lo_ok);
+        z2t = LX::ldq(p + m + 2, 0, ok2 && hi_ok);
+      }
+      a0 = fmaf(wA, z0b, a0), b0 = fmaf(wA, z1b, b0), c0 = fmaf(wA, z1t, c0), d0 = fmaf(wA, z0t, d0);
+      a1 = fmaf(wB, z1b, a1), b1 = fmaf(wB, z2b, b1), c1 = fmaf(wB, z2t, c1), d1 = fmaf(wB, z1t, d1);
+    }
+    // features; cells outside the grid of cells carry none
+    float AA = cellA ? 0.5f * (a0 - c0) : 0.f, BA = cellA ? 0.5f * (b0 - d0) : 0.f;
+    float CA = cellA ? ((a0 + c0) - (b0 + d0)) * (1.f / 6.f) : 0.f;
+    float AB = cellB ? 0.5f * (a1 - c1) : 0.f, BB = cellB ? 0.5f * (b1 - d1) : 0.f;
+    float CB = cellB ? ((a1 + c1) - (b1 + d1)) * (1.f / 6.f) : 0.f;
+    if (out_row) {
+      // cell B (this row and the previous one) seen from node cx0 + 2: sent to the right neighbour
+      const float u = (BB - CB) + (CBp - ABp);
+      const float ul = __shfl_up_sync(0xffffffffu, u, 1);
+      const float yA = ((AA + CA) - (BAp + CAp)) + ul;                       // node (cx0, cy)
+      const float yB = ((AB + CB) - (BBp + CBp)) + ((BA - CA) + (CAp - AAp));  // node (cx0 + 1, cy)
+      if (outA) Store<TYS>::put(a.Y, a.ylo, (size_t)(i - a.ybase) * a.Nx + sA, E::f(rvA, yA));
+      if (outB) Store<TYS>::put(a.Y, a.ylo, (size_t)(i - a.ybase) * a.Nx + sA + 1, E::f(rvB, yB));
+    }
+    AAp = AA, BAp = BA, CAp = CA, ABp = AB, BBp = BB, CBp = CB;
+  }
+}
+
 template <class AR, typename TXS, typename TYS, typename TRS>
 int launch_t(sg_ctx* h, ApplyArgs& a) {
+  if constexpr (std::is_same<AR, ArF32>::value && !std::is_same<TXS, DFS>::value) {
+    if (h->n >= 5) {
+      a.nwx = (h->m + 60) / 62;                // warp w finishes nodes up to 62 w + 63
+      long gy;
+      for (;;) {
+        a.nstrips = (h->m + a.strip - 1) / a.strip;
+        gy = ((long)a.nwx * a.nstrips + WARPS - 1) / WARPS;
+        if (gy <= 65535) break;
+        a.strip *= 2;
+      }
+      k_apply_f32x2<TXS, TYS, TRS><<<dim3((unsigned)a.nrows, (unsigned)gy), NT, 0, h->stream>>>(a);
+      SG_CUDA(h, cudaGetLastError());
+      count_launch(h);
+      return SG_OK;
+    }
+  }
   a.nwx = (h->m + 30) / 31;
   long gy;
   for (;;) {                                 // taller strips when the grid would exceed 65535 CTAs per row
@@ -467,6 +612,12 @@ int pick_x(sg_ctx* h, ApplyArgs& a, int xprec, int yprec, int rprec) {
     case SG_DF64:
       if constexpr (!std::is_same<AR, ArF64>::value) return pick_y<AR, DFS>(h, a, yprec, rprec);
       break;
+    case SG_F32Q:
+      if constexpr (std::is_same<AR, ArDF>::value) {
+        if (yprec == SG_F64 && !a.R) return launch_t<AR, QF32, double, NoR>(h, a);
+        if (yprec == SG_DF64 && !a.R) return launch_t<AR, QF32, DFS, NoR>(h, a);
+      }
+      break;
   }
   return sg_fail(h, SG_E_ARG, "apply: unsupported input precision");
 }
@@ -484,6 +635,8 @@ int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int
   a.X = X, a.xlo = xlo, a.Y = Y, a.ylo = ylo, a.R = R, a.rlo = rlo;
   a.c64 = h->coef64, a.c32 = h->coef32, a.cdf = (const df2*)h->coefdf;
   a.wdf = (const df2*)h->wdf, a.w64 = h->w64, a.ws = T.ws;
+  a.qmax = h->qcur;
+  if (xprec == SG_F32Q && !a.qmax) return sg_fail(h, SG_E_ARG, "apply: grid input without block maxima");
   a.row_ptr = T.row_ptr, a.tj = T.j, a.tk = T.k, a.g64 = T.g, a.g32 = T.gf, a.gdf = (const df2*)T.gdf;
   a.row0 = row0, a.nrows = nrows, a.ybase = ybase, a.rbase = rbase, a.n = h->n, a.m = h->m;
   a.Nx = h->Nx, a.Nc = h->Nc;

@@ -476,6 +476,116 @@ int vec_fill(sg_ctx* h, double* y, size_t N, double v) {
   return SG_OK;
 }
 
+// per-block max |z| as float bits (non-negative floats order like their bit patterns)
+__global__ void k_block_absmax(const float* __restrict__ Z, size_t Nx, unsigned* __restrict__ qmax) {
+  const float* z = Z + (size_t)blockIdx.y * Nx;
+  unsigned m = 0;
+  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(z[s])));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(qmax + blockIdx.y, m);
+}
+
+int block_absmax(sg_ctx* h, const float* Z, unsigned* qmax) {
+  SG_CUDA(h, cudaMemsetAsync(qmax, 0, sizeof(unsigned) * h->P, h->stream));
+  const int gx = (int)std::max<size_t>(1, std::min<size_t>((h->Nx + 4095) / 4096, 64));
+  k_block_absmax<<<dim3(gx, h->P), 256, 0, h->stream>>>(Z, h->Nx, qmax);
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  return SG_OK;
+}
+
+// grid value of z in a block with scale s and quantum q (SG_F32Q): (fma(z, s, 1.5 2^23) - 1.5 2^23) q,
+// exact (the difference by Sterbenz, the product a power of two times an integer below 2^22)
+__device__ __forceinline__ float qgrid_value(float z, float s, float q) {
+  return __fmul_rn(__fsub_rn(__fmaf_rn(z, s, SG_QBIAS), SG_QBIAS), q);
+}
+
+// FP64 U += sum_l y_l z'_l; grid x over the nodes of a block, grid y over the blocks
+template <int NV>
+__global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, size_t ldz, int nz,
+                           const double* __restrict__ y, size_t Nx, const unsigned* __restrict__ qmax, int P) {
+  const int b = blockIdx.y;
+  double c[NV];
+  float sc[NV], qu[NV];
+#pragma unroll
+  for (int l = 0; l < NV; ++l) {
+    c[l] = (l < nz) ? y[l] : 0.0;
+    const unsigned mb = (l < nz) ? qmax[(size_t)l * P + b] : 0u;
+    sc[l] = qgrid_scale(mb), qu[l] = qgrid_quantum(mb);
+  }
+  double* Ub = U + (size_t)b * Nx;
+  const float* Zb = Z + (size_t)b * Nx;
+  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
+    double u = Ub[s];
+#pragma unroll
+    for (int l = 0; l < NV; ++l)
+      if (l < nz) u += c[l] * (double)qgrid_value(Zb[(size_t)l * ldz + s], sc[l], qu[l]);
+    Ub[s] = u;
+  }
+}
+
+// double-float U (hi at U, lo at U + lo) += sum_l y_l z'_l
+__global__ void k_update_df_q(float* __restrict__ U, size_t lo, const float* __restrict__ Z, size_t ldz, int nz,
+                              const double* __restrict__ y, size_t Nx, const unsigned* __restrict__ qmax, int P) {
+  __shared__ df2 cs[SG_MAX_RESTART];
+  __shared__ float sc[SG_MAX_RESTART], qu[SG_MAX_RESTART];
+  const int b = blockIdx.y;
+  for (int l = threadIdx.x; l < nz; l += blockDim.x) {
+    cs[l] = df_from_double(y[l]);
+    const unsigned mb = qmax[(size_t)l * P + b];
+    sc[l] = qgrid_scale(mb), qu[l] = qgrid_quantum(mb);
+  }
+  __syncthreads();
+  float* Uh = U + (size_t)b * Nx;
+  float* Ul = Uh + lo;
+  const float* Zb = Z + (size_t)b * Nx;
+  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
+    dacc u = {Uh[s], Ul[s]};
+#pragma unroll 4
+    for (int l = 0; l < nz; ++l) dacc_fma(u, cs[l], qgrid_value(Zb[(size_t)l * ldz + s], sc[l], qu[l]));
+    const df2 r = dacc_get(u);
+    Uh[s] = r.hi, Ul[s] = r.lo;
+  }
+}
+
+int vec_update_q(sg_ctx* h, double* U, const float* Z, size_t ldz, int nz, const double* y_host, size_t N,
+                 const unsigned* qmax) {
+  int rc = ensure_reduction(h);
+  if (rc) return rc;
+  if (N != h->Nx * (size_t)h->P) return sg_fail(h, SG_E_ARG, "grid update: bad length");
+  const int gx = (int)std::max<size_t>(1, std::min<size_t>((h->Nx + 4095) / 4096, 64));
+  for (int c0 = 0; c0 < nz; c0 += 16) {
+    const int cn = std::min(16, nz - c0);
+    double* ydev = h->red_out + 2 * MAXOUT;
+    std::copy(y_host + c0, y_host + c0 + cn, h->red_host + 2 * MAXOUT);
+    SG_CUDA(h, cudaMemcpyAsync(ydev, h->red_host + 2 * MAXOUT, sizeof(double) * cn, cudaMemcpyHostToDevice, h->stream));
+    k_update_q<16><<<dim3(gx, h->P), 256, 0, h->stream>>>(U, Z + (size_t)c0 * ldz, ldz, cn, ydev, h->Nx,
+                                                          qmax + (size_t)c0 * h->P, h->P);
+    SG_CUDA(h, cudaGetLastError());
+    count_launch(h);
+    SG_CUDA(h, cudaStreamSynchronize(h->stream));      // the host staging slot is reused by the next chunk
+  }
+  return SG_OK;
+}
+
+int df_update_q(sg_ctx* h, float* U, size_t lo, const float* Z, size_t ldz, int nz, const double* y_host, size_t N,
+                const unsigned* qmax) {
+  int rc = ensure_reduction(h);
+  if (rc) return rc;
+  if (nz <= 0) return SG_OK;
+  if (nz > MAXOUT || N != h->Nx * (size_t)h->P) return sg_fail(h, SG_E_ARG, "grid df update: bad layout");
+  double* ydev = h->red_out + 2 * MAXOUT;
+  std::copy(y_host, y_host + nz, h->red_host + 2 * MAXOUT);
+  SG_CUDA(h, cudaMemcpyAsync(ydev, h->red_host + 2 * MAXOUT, sizeof(double) * nz, cudaMemcpyHostToDevice, h->stream));
+  const int gx = (int)std::max<size_t>(1, std::min<size_t>((h->Nx + 4095) / 4096, 64));
+  k_update_df_q<<<dim3(gx, h->P), 256, 0, h->stream>>>(U, lo, Z, ldz, nz, ydev, h->Nx, qmax, h->P);
+  SG_CUDA(h, cudaGetLastError());
+  count_launch(h);
+  SG_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SG_OK;
+}
+
 int vec_load(sg_ctx* h, const double* f, double w, double* F) {
   const size_t N = h->Nx * (size_t)h->P;
   k_load<<<grid_for(N), 256, 0, h->stream>>>(f, w, F, h->Nx, N);

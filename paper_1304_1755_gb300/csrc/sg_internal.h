@@ -15,6 +15,27 @@
 typedef __nv_bfloat16 bf16;
 
 #define SG_MAX_LEVELS 13
+// Internal input tag (not in the ABI): an FP32 vector read through its per-PC-block fixed-point grids.
+// Block b of the vector (N_x values) has the scale s_b = 2^(148 - e_b), e_b the biased exponent of the
+// block's max |z| (block_absmax); a value z stands for its grid value z' = rint(z s_b) / s_b, with
+// |z s_b| < 2^22.  The biased integer fma(z, s_b, 1.5 2^23) = 1.5 2^23 + rint(z s_b) is exact in FP32,
+// so differences of up to four such values are exact: the double-float operator forms its cell
+// features with plain FP32 subtractions.  Blocks with e_b <= 40 (max |z| < 2^-86) read as zero; a
+// block with a non-finite value reads as NaN.
+#define SG_F32Q 16
+#ifdef __CUDACC__
+// grid scale / quantum of a block from its max bits (see SG_F32Q); 0 for a block read as zero
+// (a non-finite max gives NaN, so a non-finite z_j stays visible to the solver's checks)
+__device__ __forceinline__ float qgrid_scale(unsigned maxbits) {
+  const int eb = (int)(maxbits >> 23);
+  return eb == 255 ? __int_as_float(0x7fc00000) : (eb <= 40 ? 0.f : __int_as_float((148 - eb + 127) << 23));
+}
+__device__ __forceinline__ float qgrid_quantum(unsigned maxbits) {
+  const int eb = (int)(maxbits >> 23);
+  return eb == 255 ? __int_as_float(0x7fc00000) : (eb <= 40 ? 0.f : __int_as_float((eb - 148 + 127) << 23));
+}
+#endif
+#define SG_QBIAS 12582912.0f   // 1.5 * 2^23
 #define SG_MAX_RESTART 64
 #define SG_NTHREADS_RED 256
 
@@ -90,6 +111,13 @@ struct sg_ctx {
   double* w64 = nullptr;                // the same weights in FP64 (or null)
   TermTable t_all, t_lower, t_upper, t_off, t_diag;   // all / lower / upper / off-diagonal / mean term
   double* pvec = nullptr;               // P doubles of device scratch (objective)
+  unsigned* qmax = nullptr;             // (SG_MAX_RESTART + 1) x P block maxima (float bits) of the z_j (SG_F32Q)
+  const unsigned* qcur = nullptr;       // the maxima of the SG_F32Q input of the next launch_apply
+  // exact lower-degree block (SG_PC_BLOCKTRI_EXACT): the degree-(p-1) handle and its inner solve settings
+  sg_ctx* child = nullptr;
+  double inner_tol = 1e-12;
+  int inner_restart = 30;
+  double* xbuf = nullptr;               // P * Nx doubles (right-hand side of the transposed inner solve)
   // multigrid hierarchy
   int nlev = 0;
   int lc = 0;                           // first level handled by the single-CTA coarse kernel
@@ -216,6 +244,14 @@ int vec_axpby(sg_ctx* h, double a, const double* x, double b, double* y, size_t 
 int vec_fill(sg_ctx* h, double* y, size_t N, double v);    // by a kernel (also for mapped host memory)
 // F = e_0 (x) (w f): F[s] = w f[s] (w f when f is null) for s < Nx, zero for the other PC blocks
 int vec_load(sg_ctx* h, const double* f, double w, double* F);
+// qmax[b] = bits of max |Z| over block b (P blocks of N_x consecutive values): the grids of SG_F32Q
+int block_absmax(sg_ctx* h, const float* Z, unsigned* qmax);
+// U += sum_l y_l z'_l with z'_l the grid values (SG_F32Q) of the FP32 z_l, block maxima qmax + l P;
+// FP64 U (vec_update_q) or double-float U with the lo array at + lo (df_update_q)
+int vec_update_q(sg_ctx* h, double* U, const float* Z, size_t ldz, int nz, const double* y_host, size_t N,
+                 const unsigned* qmax);
+int df_update_q(sg_ctx* h, float* U, size_t lo, const float* Z, size_t ldz, int nz, const double* y_host, size_t N,
+                const unsigned* qmax);
 int vec_dot_pairs(sg_ctx* h, int npairs, const double* const* xs, const void* const* ys, const int* yprecs,
                   size_t N, double* out_host);
 int vec_axpy_prec(sg_ctx* h, double a, int xprec, const void* x, double* y, size_t N);  // y += a x

@@ -16,7 +16,7 @@ F64, F32, BF16, DF64, BF16Z = 0, 1, 2, 3, 4   # BF16Z: BF16 preconditioner stora
 ARITH_F64, ARITH_DF64, ARITH_F64_DFOP = 0, 1, 2   # see sg_arith in include/sg.h
 LEGENDRE, HERMITE = 0, 1
 GMRES, FGMRES, GPCG, PCG, BGS = 0, 1, 2, 3, 4
-PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM = 0, 1, 2, 3
+PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM, PC_BLOCKTRI_EXACT = 0, 1, 2, 3, 4
 
 STATUS = {0: "SG_OK", -1: "SG_E_ARG", -2: "SG_E_ALLOC", -3: "SG_E_CUDA", -4: "SG_E_NOCONV",
           -5: "SG_E_BREAKDOWN", -6: "SG_E_NONFINITE", -7: "SG_E_TIMEOUT", -8: "SG_E_STATE"}
@@ -38,7 +38,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("precond", ctypes.c_int), ("restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("pc_prec", ctypes.c_int),
                 ("transpose", ctypes.c_int), ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int),
-                ("arith", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("inner_tol", ctypes.c_double), ("inner_restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -68,6 +68,7 @@ SIGNATURES = {
     "sg_precond_blocktri": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_precond_blockdiag": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
     "sg_precond_blocksym": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
+    "sg_precond_blocktri_exact": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_double]),
     "sg_vcycle": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_vcycle_static": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_solve": (ctypes.c_int, [VP, VP, VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
@@ -186,6 +187,13 @@ class Handle:
     def precond_blockdiag(self, R, Z, prec=F64):
         _check(lib().sg_precond_blockdiag(self.h, _ptr(R), _ptr(Z), prec), self.h)
 
+    def precond_blocktri_exact(self, R, Z, transpose=False, inner_tol=1e-12, check=True):
+        """sg_precond_blocktri_exact: the 2 x 2 form with the exact lower-degree block (FP64)."""
+        rc = lib().sg_precond_blocktri_exact(self.h, _ptr(R), _ptr(Z), int(transpose), inner_tol)
+        if check:
+            _check(rc, self.h)
+        return rc
+
     def precond_blocksym(self, R, Z, prec=F64):
         _check(lib().sg_precond_blocksym(self.h, _ptr(R), _ptr(Z), prec), self.h)
 
@@ -198,8 +206,9 @@ class Handle:
         _check(lib().sg_vcycle_static(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)
 
     def solve(self, F, U, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8, pc_prec=F64,
-              transpose=False, x0_given=False, reorth=0, arith=ARITH_F64, check=True):
-        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), int(x0_given), reorth, arith)
+              transpose=False, x0_given=False, reorth=0, arith=ARITH_F64, check=True, inner_tol=0.0, inner_restart=0):
+        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), int(x0_given), reorth, arith,
+                      inner_tol, inner_restart)
         info = SolveInfo()
         rc = lib().sg_solve(self.h, _ptr(F), _ptr(U), ctypes.byref(o), ctypes.byref(info))
         if check and rc not in (0,):
@@ -238,7 +247,7 @@ def solve_batch(handles, Fs, Us, nstreams=8, method=FGMRES, precond=PC_BLOCKTRI,
     n = len(handles)
     if len(Fs) != n or len(Us) != n:
         raise ValueError("handles, Fs and Us must have the same length")
-    o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, reorth, arith)
+    o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, reorth, arith, 0.0, 0)
     hs = (VP * n)(*[h.h for h in handles])
     fp = (VP * n)(*[_ptr(F) for F in Fs])
     up = (VP * n)(*[_ptr(U) for U in Us])

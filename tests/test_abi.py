@@ -78,6 +78,7 @@ def test_every_entry_point_rejects_a_null_handle_without_device(lib):
         lambda: lib.sg_timing_enable(None, 1),
         lambda: lib.sg_timing_read(None, ms, ln),
         lambda: lib.sg_rhs(None, None, None),
+        lambda: lib.sg_precond_blocktri_exact(None, None, None, 0, 0.0),
     ]
     for call in calls:
         assert call() == -1

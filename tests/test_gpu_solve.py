@@ -295,3 +295,40 @@ def test_df_fgmres_long_arnoldi_cycles():
     assert info.status == 0 and info.relres_true <= 1e-10
     assert info.iters > 16
     assert np.linalg.norm(host(U) - Ustar) <= 1e-6 * np.linalg.norm(Ustar)
+
+
+def test_exact_lower_block_preconditioner_matches_oracle():
+    """The 2 x 2 block-triangular preconditioner with the exact degree-(p-1) block (Sec. 4.2,
+    Theorem 1's form) against the oracle's (both inner solves to 1e-13), its transpose by the
+    duality <B^{-1} x, y> = <x, B^{-T} y>, and FGMRES with it against the direct solution."""
+    import torch
+    pr = Pair(33, 2, 3, basis.LEGENDRE, sigma=0.3)           # P = 10, A_hat: degree 2 (6 blocks)
+    R = inputs.uniform(71, pr.N)
+    ref = precond.block_tri_exact_inv(pr.sys, pr.oracle_vsolver(), R, inner_tol=1e-13)
+    Z = torch.empty(pr.N, dtype=torch.float64, device="cuda")
+    pr.h.precond_blocktri_exact(dev(R), Z, inner_tol=1e-13)
+    torch.cuda.synchronize()
+    got = host(Z)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    Y = inputs.uniform(72, pr.N)
+    ZT = torch.empty_like(Z)
+    pr.h.precond_blocktri_exact(dev(Y), ZT, transpose=True, inner_tol=1e-13)
+    torch.cuda.synchronize()
+    lhs, rhs = float(np.dot(got, Y)), float(np.dot(R, host(ZT)))
+    assert abs(lhs - rhs) <= 1e-9 * max(abs(lhs), 1e-300)
+    F = osg.rhs(pr.sys)
+    Ustar = osg.solve_direct(osg.assemble(pr.sys), F)
+    U = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
+    info = pr.h.solve(dev(F), U, method=sg.FGMRES, precond=sg.PC_BLOCKTRI_EXACT, pc_prec=sg.F64, tol=1e-12,
+                      restart=30, inner_tol=1e-13)
+    assert info.status == 0 and info.relres_true <= 1e-12
+    assert np.linalg.norm(host(U) - Ustar) <= 1e-8 * np.linalg.norm(Ustar)
+    A = osg.assemble(pr.sys)
+    solver = pr.oracle_vsolver()
+    _, its_o, _ = krylov.gmres(lambda v: A @ v,
+                               lambda r: precond.block_tri_exact_inv(pr.sys, solver, r, inner_tol=1e-13), F,
+                               tol=1e-12, restart=30, flexible=True)
+    assert abs(info.iters - its_o) <= 1
+    its_flat = pr.h.solve(dev(F), torch.zeros_like(U), method=sg.FGMRES, precond=sg.PC_BLOCKTRI, pc_prec=sg.F64,
+                          tol=1e-12, restart=30).iters
+    assert info.iters <= its_flat                          # the exact lower block is the stronger preconditioner
