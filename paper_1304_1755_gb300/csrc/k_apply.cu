@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
 // the load and address instructions per coupling of the one-cell-per-lane kernel, which leaves this
 // bandwidth-bound form issue-bound.
 template <typename TXS, typename TYS, typename TRS>
-__global__ void __launch_bounds__(NT) k_apply_f32x2(ApplyArgs a) {
+__global__ void __launch_bounds__(NT, 4) k_apply_f32x2(ApplyArgs a) {
   typedef ArF32 AR;
   typedef Load<TXS> LX;
   typedef typename LX::E XE;

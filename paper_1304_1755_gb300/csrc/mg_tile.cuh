@@ -22,10 +22,10 @@ namespace {
 constexpr int MT_THREADS = 256;
 constexpr int MD_TX = 64, MD_TY = 16;     // down: coarse tile (columns x rows)
 constexpr int MU_FX = 128;                // up: fine tile columns; rows: mu_fy<TB, TS>()
-// rows of the up tile: 32 for 2-byte storage, 16 for wider storage, 8 for FP64 arithmetic (the
-// window, g and the b/e part are staged in shared memory, which stays below 48 KB)
+// rows of the up tile: 32, or 16 for FP64 arithmetic (the two windows stay below 48 KB of shared
+// memory; a thread recomputes two window rows per RW = rows / 4 output rows)
 template <typename TB, typename TS, typename TA> constexpr int mu_fy() {
-  return sizeof(TA) == 8 ? 8 : (sizeof(TB) + sizeof(TS) <= 4 ? 32 : 16);
+  return sizeof(TA) == 8 ? 16 : 32;
 }
 
 template <typename T> __device__ __forceinline__ T zero_of() { return T(0); }
@@ -193,31 +193,31 @@ __global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// up: tile of MU_FX x MU_FY fine nodes starting at (X0, Y0) (both even), in two passes.
-// Pass 1 takes the window of fine nodes Y0-1 .. Y0+MU_FY (rows) x X0-1 .. X0+MU_FX (columns) in
-// 2 x 2 blocks: block (R, C) holds fine nodes (2R+1, 2C+1) on coarse node (R, C), (2R+1, 2C+2),
-// (2R+2, 2C+1) and (2R+2, 2C+2) between it and (R, C+1), (R+1, C), (R+1, C+1), so the bilinear
-// prolongation e = P x_c needs the same four coarse values for all four fine nodes, and stores
-// g = (c^2/3) b + (c/3) e for the whole window in shared memory.  No node needs a test: the
-// windows are zero outside the grid, and a fine node outside it (or on its boundary) only
-// interpolates coarse nodes outside it, so its b, e and g are zero.  Pass 2 adds the 3 x 3 box
-// sum of g to (2c - 3c^2) b + (1 - 3c) e = alpha g + beta b (alpha = (1 - 3c)/(c/3), beta =
-// 2c - 3c^2 - alpha c^2/3): a thread owns two fine columns and walks RW rows with the
-// horizontal three-sums in registers.
+// up: tile of MU_FX x MU_FY fine nodes starting at (X0, Y0) (both even).  The windows hold the fine
+// nodes Y0-1 .. Y0+MU_FY (rows) x X0-1 .. X0+MU_FX (columns) of b and the coarse nodes around them;
+// coarse window node (R, C) is fine window node (2R, 2C), so the bilinear prolongation e = P x_c at
+// fine window node (r, c) is x_c itself for even r and c, the mean of the two coarse neighbours along
+// an odd coordinate and of the four around it when both are odd.  No node needs a test: the windows
+// are zero outside the grid, and a fine node outside it (or on its boundary) only interpolates coarse
+// nodes outside it, so its b, e and g are zero.  The result is
+// x' = (2c - 3c^2) b + (1 - 3c) e + S9 g = alpha g + beta b + S9 g,  g = (c^2/3) b + (c/3) e,
+// alpha = (1 - 3c)/(c/3), beta = 2c - 3c^2 - alpha c^2/3.  Each thread owns two output columns and
+// walks RW + 2 window rows upwards: per row it forms g at its four columns from b and the coarse
+// row's horizontal interpolants (carried from one even row to the next), the two horizontal
+// three-sums of g, and finishes the row below once the row above it is known -- one pass over the
+// windows with the partial sums in registers.
 // OB, OC: b, x_c lie in guarded arrays (load_window may over-fetch aligned chunks).
 template <typename TB, typename TS, typename TA, typename TO = TS, bool OB = false, bool OC = false>
 __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ b, const TS* __restrict__ xc,
                                                          TO* __restrict__ x, int m, int mc, size_t ldb, size_t ldc,
                                                          size_t ldx, TA c, int tiles_x) {
-  constexpr int MU_FY = mu_fy<TB, TS, TA>(), RW = MU_FY / 4;   // tile rows, rows per warp in pass 2
+  constexpr int MU_FY = mu_fy<TB, TS, TA>(), RW = MU_FY / 4;   // tile rows, rows per thread
   constexpr int NRB = MU_FY + 2, NCB = MU_FX + 2, SWB = win_pitch<TB, NCB>();
   constexpr int NRC = MU_FY / 2 + 3, NCC = MU_FX / 2 + 3, SWC = win_pitch<TS, NCC>();
-  constexpr int BR = NRB / 2, BC = NCB / 2;      // 2 x 2 blocks of the window (BC = 65)
-  static_assert(BC == 65 && MT_THREADS == 256, "pass 1 maps 64 block columns x 4 block rows per sweep");
+  static_assert(MU_FX == 128 && MT_THREADS == 256 && RW % 2 == 0, "two columns per thread, 64 threads per row band");
   __shared__ __align__(16) TB sb[NRB * SWB];
   __shared__ __align__(16) TS sc[NRC * SWC];
   __shared__ int phb[NRB], phc[NRC];
-  __shared__ TA sg[NRB][NCB];                    // g over the window
   const int X0 = (blockIdx.x % tiles_x) * MU_FX, Y0 = (blockIdx.x / tiles_x) * MU_FY;
   load_window<TB, NRB, NCB, OB>(b + (size_t)blockIdx.y * ldb, m, Y0 - 1, X0 - 1, sb, phb);
   load_window<TS, NRC, NCC, OC>(xc + (size_t)blockIdx.y * ldc, mc, Y0 / 2 - 1, X0 / 2 - 1, sc, phc);
@@ -226,53 +226,54 @@ __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ 
   if (OB) fix_window_columns<TB, NRB, NCB>(sb, phb, X0 - 1, m);
   if (OC) fix_window_columns<TS, NRC, NCC>(sc, phc, X0 / 2 - 1, mc);
   const TA cgb = c * c / TA(3), cge = c / TA(3), cbb = TA(2) * c - TA(3) * c * c, cee = TA(1) - TA(3) * c;
-  // pass 1: block (br, bc) of the window = coarse node (Y0/2 - 1 + br, X0/2 - 1 + bc) = window
-  // coarse row br, column bc; its fine nodes are window rows 2br, 2br+1 and columns 2bc, 2bc+1
-  auto block = [&](int br, int bc) {
-    const TS* c0 = sc + br * SWC + phc[br] + bc;
-    const TS* c1 = sc + (br + 1) * SWC + phc[br + 1] + bc;
-    const TA x00 = sld<TA>(c0), x01 = sld<TA>(c0 + 1), x10 = sld<TA>(c1), x11 = sld<TA>(c1 + 1);
-    const TA h0 = TA(0.5) * (x00 + x01), v0 = TA(0.5) * (x00 + x10), q = TA(0.25) * ((x00 + x01) + (x10 + x11));
-    const TB* b0 = sb + (2 * br) * SWB + phb[2 * br] + 2 * bc;
-    const TB* b1 = sb + (2 * br + 1) * SWB + phb[2 * br + 1] + 2 * bc;
-    TA* g0 = &sg[2 * br][2 * bc];
-    TA* g1 = &sg[2 * br + 1][2 * bc];
-    g0[0] = cgb * sld<TA>(b0) + cge * x00;
-    g0[1] = cgb * sld<TA>(b0 + 1) + cge * h0;
-    g1[0] = cgb * sld<TA>(b1) + cge * v0;
-    g1[1] = cgb * sld<TA>(b1 + 1) + cge * q;
-  };
-  {
-    const int bc = threadIdx.x & 63;
-    for (int br = threadIdx.x >> 6; br < BR; br += 4) block(br, bc);
-    if (threadIdx.x < BR) block(threadIdx.x, 64);
-  }
-  __syncthreads();
-  // pass 2: thread columns k0, k0 + 1 of the tile, rows jw .. jw + RW - 1
   const TA alpha = cee / cge, beta = cbb - alpha * cgb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k0 = 64 * (warp & 1) + 2 * lane;
-  const int jw = RW * (warp >> 1);
-  const int i0 = X0 + k0, i1 = i0 + 1;
-  TA H0[RW + 2], H1[RW + 2], G0[RW + 2], G1[RW + 2];
-#pragma unroll
-  for (int k = 0; k < RW + 2; ++k) {              // window rows jw .. jw + RW + 1 = fine rows Y0 + jw - 1 ..
-    const TA* gr = &sg[jw + k][k0];               // window columns k0 .. k0 + 3 = fine i0 - 1 .. i1 + 1
-    const TA gm = gr[0], g0 = gr[1], g1 = gr[2], gp = gr[3];
-    H0[k] = (gm + g0) + g1;
-    H1[k] = (g0 + g1) + gp;
-    G0[k] = g0, G1[k] = g1;
-  }
+  const int k0 = 64 * (warp & 1) + 2 * lane;                   // window columns k0 .. k0 + 3 (k0 even)
+  const int jw = RW * (warp >> 1);                             // window rows jw .. jw + RW + 1 (jw even)
+  const int C0 = k0 / 2;                                       // coarse window columns C0 .. C0 + 2
+  // horizontal interpolants of coarse window row R at the fine window columns k0 .. k0 + 3
+  auto hrow = [&](int R, TA* hv) {
+    const TS* cr = sc + R * SWC + phc[R] + C0;
+    const TA x0 = sld<TA>(cr), x1 = sld<TA>(cr + 1), x2 = sld<TA>(cr + 2);
+    hv[0] = x0, hv[1] = TA(0.5) * (x0 + x1), hv[2] = x1, hv[3] = TA(0.5) * (x1 + x2);
+  };
+  TA hA[4];
+  int R = jw / 2;
+  hrow(R, hA);
+  TA Hm2[2] = {0, 0}, Hm1[2] = {0, 0}, gm1[2] = {0, 0}, bm1[2] = {0, 0};
+  const int i0 = X0 + k0, i1 = i0 + 1;                         // fine columns of the outputs
   TO* xb = x + (size_t)blockIdx.y * ldx;
 #pragma unroll
-  for (int q = 0; q < RW; ++q) {
-    const int j = Y0 + jw + q;
-    if (j < m) {
-      const TB* br = sb + (jw + q + 1) * SWB + phb[jw + q + 1] + k0 + 1;   // b at i0, i1
-      TO* op = xb + (size_t)j * m;
-      if (i0 < m) st_as<TO, TA>(op + i0, alpha * G0[q + 1] + beta * sld<TA>(br) + ((H0[q] + H0[q + 1]) + H0[q + 2]));
-      if (i1 < m) st_as<TO, TA>(op + i1, alpha * G1[q + 1] + beta * sld<TA>(br + 1) + ((H1[q] + H1[q + 1]) + H1[q + 2]));
+  for (int k = 0; k < RW + 2; ++k) {
+    const int r = jw + k;
+    TA e[4];
+    if ((k & 1) == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) e[q] = hA[q];
+    } else {
+      TA hB[4];
+      hrow(R + 1, hB);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) e[q] = TA(0.5) * (hA[q] + hB[q]), hA[q] = hB[q];
+      ++R;
     }
+    const TB* br = sb + r * SWB + phb[r] + k0;
+    TA bv[4], g[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bv[q] = sld<TA>(br + q), g[q] = cgb * bv[q] + cge * e[q];
+    const TA H0 = (g[0] + g[1]) + g[2], H1 = (g[1] + g[2]) + g[3];
+    if (k >= 2) {                                               // window row r - 1 = fine row Y0 + r - 2
+      const int j = Y0 + r - 2;
+      if (j < m) {
+        TO* op = xb + (size_t)j * m;
+        if (i0 < m) st_as<TO, TA>(op + i0, alpha * gm1[0] + beta * bm1[0] + ((Hm2[0] + Hm1[0]) + H0));
+        if (i1 < m) st_as<TO, TA>(op + i1, alpha * gm1[1] + beta * bm1[1] + ((Hm2[1] + Hm1[1]) + H1));
+      }
+    }
+    Hm2[0] = Hm1[0], Hm2[1] = Hm1[1];
+    Hm1[0] = H0, Hm1[1] = H1;
+    gm1[0] = g[1], gm1[1] = g[2];
+    bm1[0] = bv[1], bm1[1] = bv[2];
   }
 }
 }  // namespace
