@@ -224,6 +224,35 @@ def timed_solves(h, F, U, opts, steps, stream):
     return e0.elapsed_time(e1) / steps, info
 
 
+def run_apply_only(args, wl):
+    """The SG apply Y = A X of the workload's problem on its own: median CUDA-event time of
+    sg_apply with FP32, FP64 and double-float storage (the same launches as the operator of the
+    solves), algorithmic bytes per launch and the fraction of the measured HBM bandwidth."""
+    import torch
+    from paper_1304_1755_gb300 import build as B
+    from paper_1304_1755_gb300 import sg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    if not os.path.exists(sg.LIB_PATH):
+        B.build()
+    coef, _ = build_problem(wl)
+    h = sg.Handle(wl["n"], wl["M"], wl["p"], wl["family"], coef, stream=torch.cuda.current_stream())
+    h.autotune()
+    N = h.P * h.Nx
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    rows = {}
+    for name, prec, dt, sb, n_el in (("f32", sg.F32, torch.float32, 4, N), ("f64", sg.F64, torch.float64, 8, N),
+                                     ("df64", sg.DF64, torch.float32, 8, 2 * N)):
+        X = torch.rand(n_el, dtype=dt, device="cuda") * 2 - 1
+        Y = torch.empty_like(X)
+        ms = time_apply(h, X, Y, prec, reps=max(args.steps, 1), warm=max(args.warmup, 1))
+        b = k1_bytes(wl, sb, sb)
+        rows[name] = {"ms": round(ms, 4), "gbs": round(b / (ms * 1e-3) / 1e9, 1),
+                      "frac_of_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4), "bytes": b}
+        del X, Y
+    h.close()
+    return {"metric": "SG-apply HBM GB/s", "config": {"workload": wl["name"], "unknowns": N}, "apply": rows}
+
+
 def run_ours(args, wl, rank, world):
     import numpy as np
     import torch
@@ -661,15 +690,26 @@ def run_c5(args, wl, rank, world):
     def one_at_a_time():
         return [h.solve(F, U, **opts) for h, F, U in zip(hs, Fs, Us)]
 
-    def batched():
+    def batched_streams():
         return sg.solve_batch(hs, Fs, Us, nstreams=wl["nstreams"], **opts)
+
+    # the batch's CUDA graphs (every system's restart cycle with its Arnoldi control on the device, the
+    # systems side by side) are built once, as set-up; a solve is one launch of the start graph and one
+    # launch of the cycle graph per restart cycle of the whole batch
+    for h in hs:
+        h.timing_read()                                        # launch counters from zero
+    t0 = time.perf_counter()
+    batch = sg.Batch(hs, Fs, Us, **opts)
+    graph_build_s = time.perf_counter() - t0
+    graph_kernels = sum(sum(h.timing_read()[1]) for h in hs)   # kernel nodes captured into the graphs
+
+    def batched():
+        return batch.solve()
 
     for _ in range(args.warmup):
         one_at_a_time()
         batched()
     torch.cuda.synchronize()
-    for h in hs:
-        h.timing_enable(True)
     barrier()
     with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
@@ -679,6 +719,16 @@ def run_c5(args, wl, rank, world):
         barrier()
         t_batch = (time.perf_counter() - t0) / args.steps
     clocks = clk.summary()
+    batch.close()
+    batched_streams()
+    torch.cuda.synchronize()
+    for h in hs:
+        h.timing_enable(True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        infos_s = batched_streams()
+    torch.cuda.synchronize()
+    t_streams = (time.perf_counter() - t0) / args.steps
     ph = [h.timing_read() for h in hs]
     for h in hs:
         h.timing_enable(False)
@@ -687,18 +737,23 @@ def run_c5(args, wl, rank, world):
         infos1 = one_at_a_time()
     torch.cuda.synchronize()
     t_seq = (time.perf_counter() - t0) / args.steps
-    t_batch, t_seq = max_over_ranks([t_batch, t_seq])
-    launches = sum(sum(l) for _, l in ph) // args.steps
+    t_batch, t_streams, t_seq = max_over_ranks([t_batch, t_streams, t_seq])
     op_ms = sum(m[0] for m, _ in ph) / args.steps
     op_launches = sum(l[0] for _, l in ph) // args.steps
     # end to end through the C ABI with host (pinned) buffers: sg_solve stages them per system
     Fh = [F.cpu().pin_memory() for F in Fs]
     Uh = [torch.zeros_like(F).pin_memory() for F in Fh]
+    batch = sg.Batch(hs, Fs, Us, **opts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sg.solve_batch(hs, [F.numpy() for F in Fh], [U.numpy() for U in Uh], nstreams=wl["nstreams"], **opts)
+    for F, Fp in zip(Fs, Fh):                                  # host -> device, the batch solve, device -> host
+        F.copy_(Fp, non_blocking=True)
+    batch.solve()
+    for U, Up in zip(Us, Uh):
+        Up.copy_(U, non_blocking=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    batch.close()
     nbytes = 8 * unknowns
     out = {
         "metric": C5_METRIC,
@@ -709,17 +764,26 @@ def run_c5(args, wl, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 Krylov (double-float outer operator), preconditioner f32",
         "data": "synthetic (seeded uneven batch: KL coefficients, Legendre chaos, f = 1)",
-        "config": {"workload": wl["name"], "systems": len(hs), "unknowns": unknowns, "nstreams": wl["nstreams"],
+        "config": {"workload": wl["name"], "systems": len(hs), "unknowns": unknowns,
+                   "batched_form": "one CUDA graph: per system a chain of conditional steps with the Arnoldi "
+                                   "control on the device; one launch per restart cycle of the whole batch",
                    "sigma_lowered": sum(1 for s in systems if s["sigma"] < s["sigma_drawn"]),
                    "l2": "working set of the batch larger than L2, no flush"},
         "one_at_a_time": {"value": round(world * unknowns / t_seq, 1), "unit": "unknowns/s",
                           "ms_per_step": round(t_seq * 1e3, 3)},
+        "host_streams": {"value": round(world * unknowns / t_streams, 1), "unit": "unknowns/s",
+                         "ms_per_step": round(t_streams * 1e3, 3), "nstreams": wl["nstreams"],
+                         "iterations_equal": all(i.iters == j.iters for i, j in zip(infos_s, infos1))},
         "batch_speedup": round(t_seq / t_batch, 3),
         "iterations": [i.iters for i in infos],
+        "restart_cycles_max": max(i.restarts for i in infos) + 1,
         "relres_true_max": max(i.relres_true for i in infos),
-        "agree_with_one_at_a_time": all(i.iters == j.iters for i, j in zip(infos, infos1)),
+        "iterations_within_one_of_one_at_a_time": all(abs(i.iters - j.iters) <= 1 for i, j in zip(infos, infos1)),
         "autotune_s": round(tune_s, 3),
-        "gpu_launches": int(launches),
+        "graph_build_s": round(graph_build_s, 3),
+        "graph_launches_per_step": 1 + max(i.restarts for i in infos) + 1,
+        "gpu_launches": int(graph_kernels),
+        "gpu_launches_note": "kernel nodes in the batch's two graphs (the steps a system skips are not run)",
         "e2e": {"value": round(world * unknowns / t_e2e, 1), "unit": "unknowns/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "clocks": clocks,
@@ -835,6 +899,9 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--pc-prec", choices=["f64", "f32", "bf16", "bf16z"], default=None,
                     help="override the workload's preconditioner storage precision")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time only the SG apply (FP32, FP64 and double-float sg_apply) of the workload's "
+                         "problem and print its line (for kernel profiling)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.pc_prec is not None:
@@ -892,6 +959,9 @@ def main():
                                             "sample": smp.describe(dt, its)},
                               e2e={"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
                                    "d2h_bytes_per_step": 0})))
+        return
+    if args.apply_only:
+        print(json.dumps(run_apply_only(args, wl)))
         return
     if world > 1:
         import torch

@@ -271,6 +271,31 @@ int sg_solve(sg_handle h, const double* F, double* U, const sg_solve_opts* opts,
 int sg_solve_batch(sg_handle* hs, const double* const* F, double* const* U, int nsys, const sg_solve_opts* opts,
                    sg_solve_info* infos, int nstreams);
 
+/* The same batch as sg_solve_batch, solved in one CUDA graph (the batched form of the method's solve,
+ * Sec. 4.2 / 6): every system's FGMRES restart cycle, with its Arnoldi scalars (Gram-Schmidt
+ * coefficients, Hessenberg column, Givens rotations, convergence test, back substitution) computed by
+ * one-thread kernels on the device and every further step behind a conditional graph node that the
+ * previous step opens, is a chain of nodes; the chains of all systems sit side by side in one graph,
+ * and one launch of it runs one restart cycle of the whole batch.  The call builds and instantiates the
+ * graph, launches it until no system is running (normally once or twice), and reads each system's
+ * outcome once per launch.  FGMRES with an FP64 basis only (arith SG_ARITH_F64, or SG_ARITH_F64_DFOP
+ * with an SG_F32, SG_BF16 or SG_BF16Z preconditioner), restart 1..32, x0_given = 0, reorth = 0; F[s] and
+ * U[s] device FP64; handles distinct, on the current device, and not used by other calls meanwhile (each
+ * handle's stream is restored afterwards).  infos (may be NULL) as in sg_solve_batch.  Returns SG_OK or
+ * the first failing system's status; SG_E_ARG for unsupported options before any work. */
+int sg_solve_batch_graph(sg_handle* hs, const double* const* F, double* const* U, int nsys, const sg_solve_opts* opts,
+                         sg_solve_info* infos);
+/* sg_solve_batch_graph in three calls, for a batch solved repeatedly: sg_batch_create does the checks,
+ * the workspaces and the graph construction (same arguments as sg_solve_batch_graph; *out receives the
+ * batch); sg_batch_solve solves it (U[s] overwritten, infos as above); sg_batch_destroy releases the
+ * graphs.  Between create and destroy the handles' workspaces must not change: a solve with a larger
+ * restart or another precision on one of them makes sg_batch_solve return SG_E_STATE. */
+typedef struct sg_batch_ctx* sg_batch;
+int sg_batch_create(sg_handle* hs, const double* const* F, double* const* U, int nsys, const sg_solve_opts* opts,
+                    sg_batch* out);
+int sg_batch_solve(sg_batch b, sg_solve_info* infos);
+void sg_batch_destroy(sg_batch b);
+
 /* Choose the operator kernel's tile (the number of grid rows a warp walks) for this
  * problem by timing the candidates 4, 8, 16, 32 and 64 on the device (a tuning step of
  * this implementation; the paper has no counterpart).  which: bit 0 FP64 arithmetic,

@@ -685,6 +685,11 @@ void destroy_ctx(sg_ctx* h) {
 }
 }  // namespace
 
+int apply_precond_ext(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec, int transpose) {
+  return apply_precond(h, pc, rprec, R, Z, prec, transpose);
+}
+int ensure_krylov_ext(sg_ctx* h, int nv, int nz, int zprec, int layout) { return ensure_krylov(h, nv, nz, zprec, layout); }
+
 int sg_fail(sg_ctx* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   else {

@@ -451,18 +451,17 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
 }
 
 // FP32 arithmetic, two cells per lane.  Lane l of a warp owns the cells cx0 = X + 2l and cx0 + 1
-// of each cell row (X = 62 w, even, so the cells' coefficient pair is one aligned 8-byte load;
-// consecutive warps overlap by two cells) and walks a strip of cell rows
-// for one output row i.  Per cell row and coupling it loads its two node columns in the two node rows
-// of the cell row (the third column, cx0 + 2, comes from the right lane by a shuffle; lane 31 loads
-// it), loads the two cells' coefficients as one 8-byte pair (the cell rows have an even length) and
-// mixes the corners with four multiply-adds per cell.  It finishes node cx0 + 1 from its own two
-// cells in this and the previous cell row, and node cx0 from its first cell and the left lane's
-// second cell, whose contribution arrives in one shuffle.  Lane 0 only supplies its cells (node
-// X + 1 is the previous warp's lane 31's), except in the first warp, whose lane 0 finishes node 1;
-// so warp w writes nodes 62 w + 2 .. 62 w + 63 once each.  About half
-// the load and address instructions per coupling of the one-cell-per-lane kernel, which leaves this
-// bandwidth-bound form issue-bound.
+// of each cell row (X = 62 w, even, so the cells' coefficient pair is one aligned 8-byte load) and
+// walks a strip of cell rows for one output row i.  Per cell row and coupling it loads its two node
+// columns in the two node rows of the cell row (the third column, cx0 + 2, comes from the right lane
+// by a shuffle), loads the two cells' coefficients as one 8-byte pair (the cell rows have an even
+// length) and mixes the corners with four multiply-adds per cell.  It finishes node cx0 + 1 from its
+// own two cells in this and the previous cell row, and node cx0 from its first cell and the left
+// lane's second cell, whose contribution arrives in one shuffle.  The edge lanes only half count:
+// lane 0 has no left lane (it finishes node X + 1 only) and lane 31 no right column (its second cell
+// is incomplete, it finishes node X + 62 only), so warp w writes nodes 62 w + 1 .. 62 w + 62 once
+// each with no extra loads.  About half the load and address instructions per coupling of the
+// one-cell-per-lane kernel.
 template <typename TXS, typename TYS, typename TRS>
 __global__ void __launch_bounds__(NT, 4) k_apply_f32x2(ApplyArgs a) {
   typedef ArF32 AR;
@@ -485,14 +484,13 @@ __global__ void __launch_bounds__(NT, 4) k_apply_f32x2(ApplyArgs a) {
   if (gw >= a.nwx * a.nstrips) return;
   const int lane = threadIdx.x & 31;
   const int n = a.n, m = a.m;
-  const int wx = gw % a.nwx;
-  const int cx0 = 62 * wx + 2 * lane;                       // first cell (= vertex column of its SW corner)
+  const int cx0 = 62 * (gw % a.nwx) + 2 * lane;            // first cell (= vertex column of its SW corner)
   const int cy0 = a.strip * (gw / a.nwx);
   const int cy1 = min(cy0 + a.strip, n - 2);
-  // columns cx0, cx0 + 1, cx0 + 2 interior?
-  const bool ok0 = cx0 >= 1 && cx0 <= n - 2, ok1 = cx0 + 1 <= n - 2, ok2 = cx0 + 2 <= n - 2;
+  // columns cx0, cx0 + 1 interior?
+  const bool ok0 = cx0 >= 1 && cx0 <= n - 2, ok1 = cx0 + 1 <= n - 2;
   const bool cellA = cx0 <= n - 2, cellB = cx0 + 1 <= n - 2;   // cells inside the grid of cells
-  const bool outA = lane >= 1 && ok0, outB = ok1 && (lane >= 1 || wx == 0);   // nodes cx0, cx0 + 1 finished here
+  const bool outA = lane >= 1 && ok0, outB = lane <= 30 && ok1;   // nodes cx0, cx0 + 1 finished here
   const int cxw = min(cx0, n - 3);                             // weight pair (cells n - 3, n - 2 at most; n - 3 is even)
   const bool wshift = cxw != cx0;                              // only past the last cell pair (weights unused)
   float AAp = 0.f, BAp = 0.f, CAp = 0.f, ABp = 0.f, BBp = 0.f, CBp = 0.f;   // previous cell row's features
@@ -516,11 +514,7 @@ __global__ void __launch_bounds__(NT, 4) k_apply_f32x2(ApplyArgs a) {
       const float wA = (wshift ? cw.y : cw.x) * g, wB = cw.y * g;
       const float z0b = LX::ldq(p, 0, ok0 && lo_ok), z1b = LX::ldq(p + 1, 0, ok1 && lo_ok);
       const float z0t = LX::ldq(p + m, 0, ok0 && hi_ok), z1t = LX::ldq(p + m + 1, 0, ok1 && hi_ok);
-      float z2b = __shfl_down_sync(0xffffffffu, z0b, 1), z2t = __shfl_down_sync(0xffffffffu, z0t, 1);
-      if (lane == 31) {
-        z2b = LX::ldq(p + 2, 0, ok2 && lo_ok);
-        z2t = LX::ldq(p + m + 2, 0, ok2 && hi_ok);
-      }
+      const float z2b = __shfl_down_sync(0xffffffffu, z0b, 1), z2t = __shfl_down_sync(0xffffffffu, z0t, 1);
       a0 = fmaf(wA, z0b, a0), b0 = fmaf(wA, z1b, b0), c0 = fmaf(wA, z1t, c0), d0 = fmaf(wA, z0t, d0);
       a1 = fmaf(wB, z1b, a1), b1 = fmaf(wB, z2b, b1), c1 = fmaf(wB, z2t, c1), d1 = fmaf(wB, z1t, d1);
     }
@@ -546,7 +540,7 @@ template <class AR, typename TXS, typename TYS, typename TRS>
 int launch_t(sg_ctx* h, ApplyArgs& a) {
   if constexpr (std::is_same<AR, ArF32>::value && !std::is_same<TXS, DFS>::value) {
     if (h->n >= 5) {
-      a.nwx = (h->m + 60) / 62;                // warp w finishes nodes up to 62 w + 63
+      a.nwx = (h->m + 61) / 62;                // warp w finishes nodes 62 w + 1 .. 62 w + 62
       long gy;
       for (;;) {
         a.nstrips = (h->m + a.strip - 1) / a.strip;

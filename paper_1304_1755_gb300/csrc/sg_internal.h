@@ -212,6 +212,10 @@ void build_terms(const sg_ctx* h, int which, std::vector<int>& row_ptr, std::vec
                  std::vector<int>& tk, std::vector<double>& tg);
 void galerkin_stencils(int n0, int nlev, const double* abar_cells, std::vector<std::vector<double>>& st);
 
+// api.cu: the preconditioner dispatch and the Krylov workspace of sg_solve (layout 0: FP64 basis)
+int apply_precond_ext(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec, int transpose);
+int ensure_krylov_ext(sg_ctx* h, int nv, int nz, int zprec, int layout);
+
 // k_apply.cu
 // which: 0 = all terms (Y = A X), 1 = lower terms, 2 = upper terms, 3 = off-diagonal terms,
 // 4 = the mean term only (Y = (I (x) K_0) X).

@@ -74,6 +74,12 @@ SIGNATURES = {
     "sg_solve": (ctypes.c_int, [VP, VP, VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "sg_solve_batch": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_int,
                                       ctypes.POINTER(SolveOpts), VP, ctypes.c_int]),
+    "sg_solve_batch_graph": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_int,
+                                            ctypes.POINTER(SolveOpts), VP]),
+    "sg_batch_create": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_int,
+                                       ctypes.POINTER(SolveOpts), ctypes.POINTER(VP)]),
+    "sg_batch_solve": (ctypes.c_int, [VP, VP]),
+    "sg_batch_destroy": (None, [VP]),
     "sg_autotune": (ctypes.c_int, [VP, ctypes.c_int]),
     "sg_objective": (ctypes.c_int, [VP, VP, DP, VP]),
     "sg_adjoint_gradients": (ctypes.c_int, [VP, VP, VP, ctypes.c_double, VP, DP]),
@@ -258,3 +264,61 @@ def solve_batch(handles, Fs, Us, nstreams=8, method=FGMRES, precond=PC_BLOCKTRI,
         raise SGError(rc, f"sg_solve_batch: systems {bad} failed" + (
             f": {lib().sg_last_error(handles[bad[0]].h).decode()}" if bad else ""))
     return list(infos)
+
+
+def solve_batch_graph(handles, Fs, Us, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8,
+                      pc_prec=F64, transpose=False, arith=ARITH_F64, check=True):
+    """sg_solve_batch_graph: the batch solved in one CUDA graph (device-side Arnoldi control, one launch
+    per restart cycle of all systems); returns one SolveInfo per system."""
+    n = len(handles)
+    if len(Fs) != n or len(Us) != n:
+        raise ValueError("handles, Fs and Us must have the same length")
+    o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, 0, arith, 0.0, 0)
+    hs = (VP * n)(*[h.h for h in handles])
+    fp = (VP * n)(*[_ptr(F) for F in Fs])
+    up = (VP * n)(*[_ptr(U) for U in Us])
+    infos = (SolveInfo * n)()
+    rc = lib().sg_solve_batch_graph(hs, fp, up, n, ctypes.byref(o), ctypes.cast(infos, VP))
+    if check and rc != 0:
+        bad = [i for i in range(n) if infos[i].status != 0]
+        raise SGError(rc, f"sg_solve_batch_graph: systems {bad} failed" + (
+            f": {lib().sg_last_error(handles[bad[0] if bad else 0].h).decode()}"))
+    return list(infos)
+
+
+class Batch:
+    """sg_batch_create / sg_batch_solve / sg_batch_destroy: a batch whose CUDA graphs are built once and
+    launched for every solve (the handles, F and U fixed at creation)."""
+
+    def __init__(self, handles, Fs, Us, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8,
+                 pc_prec=F64, transpose=False, arith=ARITH_F64):
+        n = len(handles)
+        if len(Fs) != n or len(Us) != n:
+            raise ValueError("handles, Fs and Us must have the same length")
+        self.handles, self.n = handles, n
+        self._keep = (Fs, Us)
+        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, 0, arith, 0.0, 0)
+        hs = (VP * n)(*[h.h for h in handles])
+        fp = (VP * n)(*[_ptr(F) for F in Fs])
+        up = (VP * n)(*[_ptr(U) for U in Us])
+        b = VP()
+        _check(lib().sg_batch_create(hs, fp, up, n, ctypes.byref(o), ctypes.byref(b)), handles[0].h)
+        self.b = b
+
+    def solve(self, check=True):
+        infos = (SolveInfo * self.n)()
+        rc = lib().sg_batch_solve(self.b, ctypes.cast(infos, VP))
+        if check and rc != 0:
+            raise SGError(rc, lib().sg_last_error(self.handles[0].h).decode())
+        return list(infos)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().sg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -79,10 +79,14 @@ def test_every_entry_point_rejects_a_null_handle_without_device(lib):
         lambda: lib.sg_timing_read(None, ms, ln),
         lambda: lib.sg_rhs(None, None, None),
         lambda: lib.sg_precond_blocktri_exact(None, None, None, 0, 0.0),
+        lambda: lib.sg_solve_batch_graph(None, None, None, 1, ctypes.byref(o), None),
+        lambda: lib.sg_batch_create(None, None, None, 1, ctypes.byref(o), ctypes.byref(ctypes.c_void_p())),
+        lambda: lib.sg_batch_solve(None, None),
     ]
     for call in calls:
         assert call() == -1
     lib.sg_destroy(None)
+    lib.sg_batch_destroy(None)
 
 
 def test_batch_rejects_a_repeated_handle_without_device(lib):
