@@ -14,7 +14,8 @@ tolerance 1e-8 on the true relative residual, recomputed in IEEE FP64.  A step i
 full solve from U = 0 with F resident in HBM.  Every vector is 1.76 GB (> L2), so no
 L2 flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1|c4|c5|c3s|table3]
+    python bench.py [--gpus N] [--steps K] [--warmup W]
+                    [--workload c3|c2|c1|c4|c5|c3s|table3|table3p1|table3p1rb]
                     [--arith f64dfop|f64|df64] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
@@ -52,6 +53,11 @@ WORKLOADS = {
     # point Gauss-Seidel)
     "table3": dict(n=65, M=6, p=4, family=0, sigmas=(0.1, 0.2, 0.3, 0.4), tol=1e-10, restart=10, nu=2,
                    name="paper_table3_65sq_M6_legendre_p4_tol1e-10"),
+    # the same with the paper's own discretisation: P1 triangles and point Gauss-Seidel V(2,2)
+    "table3p1": dict(n=65, M=6, p=4, family=0, sigmas=(0.1, 0.2, 0.3, 0.4), tol=1e-10, restart=10, nu=2,
+                     elements=1, gs_order=0, name="paper_table3_p1_65sq_M6_legendre_p4_gs_lex_tol1e-10"),
+    "table3p1rb": dict(n=65, M=6, p=4, family=0, sigmas=(0.1, 0.2, 0.3, 0.4), tol=1e-10, restart=10, nu=2,
+                       elements=1, gs_order=1, name="paper_table3_p1_65sq_M6_legendre_p4_gs_redblack_tol1e-10"),
     # adjoint gradient of J = E[int u] + Var[int u] / 2 w.r.t. the per-cell mean and sigma.  At sigma =
     # 0.4 the 257^2 system (lognormal mean, not coercive at the xi-box corners) makes restarted
     # GMRES(30) stagnate near 1e-6 in FP64 as well, so the timed gradient uses sigma = 0.3; the
@@ -464,9 +470,9 @@ def c2_sweep(wl, stream):
 
 def run_table3(args, wl, rank, world):
     """The five methods of the paper's Table 3 (B-GS, BD-PCG, BT-GPCG, BT-GMRes(10), BS-PCG), FP64, on
-    this repository's Q1 / damped-Jacobi V(2,2) discretisation of the paper's test problem; iteration
-    counts and device times, with the paper's counts (P1 triangles, point Gauss-Seidel V(2,2), MATLAB)
-    beside them as context."""
+    the paper's test problem with Q1 elements and a damped-Jacobi V(2,2) (table3) or with the paper's
+    own P1 triangles and point Gauss-Seidel V(2,2), lexicographic or red-black (table3p1, table3p1rb);
+    iteration counts and device times, with the paper's counts (P1, MATLAB) beside them as context."""
     import numpy as np
     import torch
     from paper_1304_1755_gb300 import build as B
@@ -488,9 +494,11 @@ def run_table3(args, wl, rank, world):
                ("BT-GPCG", sg.GPCG, sg.PC_BLOCKTRI), ("BT-GMRes", sg.GMRES, sg.PC_BLOCKTRI),
                ("BS-PCG", sg.PCG, sg.PC_BLOCKSYM)]
     rows, total_ms = [], 0.0
+    p1 = wl.get("elements", 0) == sg.P1
     for si, sigma in enumerate(wl["sigmas"]):
-        coef, _ = sg.sg_kl_coef(n, M, sigma)
-        h = sg.Handle(n, M, p, wl["family"], coef, nu1=wl["nu"], nu2=wl["nu"], stream=stream)
+        coef, _ = (sg.sg_kl_coef_p1 if p1 else sg.sg_kl_coef)(n, M, sigma)
+        h = sg.Handle(n, M, p, wl["family"], coef, nu1=wl["nu"], nu2=wl["nu"], stream=stream,
+                      elements=wl.get("elements", 0), gs_order=wl.get("gs_order", 0))
         F = torch.empty(h.P * h.Nx, dtype=torch.float64, device="cuda")
         h.rhs(F, fdev)
         for name, meth, pc in methods:
@@ -515,7 +523,10 @@ def run_table3(args, wl, rank, world):
             "value": round(total_ms / 1e3, 4), "unit": "s (all 20 solves)", "n_gpus": world, "steps": 1,
             "warmup": 1, "ms_per_step": round(total_ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (the paper's f and KL setting)",
-            "config": {"workload": wl["name"], "smoother": "damped Jacobi V(2,2)", "elements": "Q1"},
+            "config": {"workload": wl["name"],
+                       "smoother": (("lexicographic" if wl["gs_order"] == 0 else "red-black") +
+                                    " point Gauss-Seidel V(2,2)") if p1 else "damped Jacobi V(2,2)",
+                       "elements": "P1" if p1 else "Q1"},
             "rows": rows, "gpu_launches": None, "e2e": None, "clocks": None, "roofline": None}
 
 
@@ -912,7 +923,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        if args.workload in ("table3", "c3s"):
+        if args.workload in ("table3", "table3p1", "table3p1rb", "c3s"):
             print(json.dumps({"impl": "reference", "unavailable": f"{args.workload} is a context/profiling workload "
                                                                    "without a reference timing"}))
             return
@@ -966,7 +977,7 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload == "table3":
+    if args.workload in ("table3", "table3p1", "table3p1rb"):
         out = run_table3(args, wl, rank, world)
         if rank == 0:
             print(json.dumps(out))

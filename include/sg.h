@@ -75,6 +75,23 @@ typedef enum { SG_F64 = 0, SG_F32 = 1, SG_BF16 = 2, SG_DF64 = 3, SG_BF16Z = 4 } 
  *     FGMRES with an SG_F32, SG_BF16 or SG_BF16Z preconditioner. */
 typedef enum { SG_ARITH_F64 = 0, SG_ARITH_DF64 = 1, SG_ARITH_F64_DFOP = 2 } sg_arith;
 typedef enum { SG_LEGENDRE = 0, SG_HERMITE = 1 } sg_family;
+/* Spatial discretisation.  SG_Q1: bilinear elements on the square cells (the configurations' form).
+ * SG_P1: the paper's own discretisation (Sec. 6): every cell cut by its SW-NE diagonal into a lower-
+ * right and an upper-left right triangle, linear elements, the coefficient constant per triangle, so
+ * each K_k is a 5-point stencil with edge weights; its V-cycle smooths with point Gauss-Seidel
+ * (forward sweeps before, backward after the coarse correction, nu1 / nu2 of them; lexicographic or
+ * red-black order, sg_gs_order),
+ * prolongs by linear interpolation on the nested triangulations and restricts by its transpose.  SG_P1
+ * handles take per-triangle coefficients, need a mean coefficient of exactly 1 (every coarse operator
+ * is then the 5-point Laplacian) and compute in FP64 only: operators and preconditioners with
+ * SG_F64, solves with pc_prec = SG_F64 and arith = SG_ARITH_F64; the allocation-free V-cycle, the
+ * tile autotuner and the adjoint gradients are Q1-only. */
+typedef enum { SG_Q1 = 0, SG_P1 = 1 } sg_elements;
+/* Point Gauss-Seidel order of the SG_P1 V-cycle.  SG_GS_LEX: lexicographic (x fastest); the forward
+ * sweep updates a node after its west and south neighbours, the backward sweep in the reverse order.
+ * SG_GS_RB: red-black, colour (x + y) mod 2; the forward sweep updates colour 0 then colour 1, the
+ * backward sweep colour 1 then colour 0 (both forms make the cycle a symmetric operator). */
+typedef enum { SG_GS_LEX = 0, SG_GS_RB = 1 } sg_gs_order;
 /* SG_BGS: the stationary block Gauss-Seidel iteration U += B_T^{-1}(F - A U) (Sec. 4.2). */
 typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3, SG_BGS = 4 } sg_method;
 /* SG_PC_BLOCKSYM: B_S = B_T diag(A)^{-1} B_T^T, the symmetric block Gauss-Seidel
@@ -95,10 +112,14 @@ typedef enum {
 /* One SG problem (Sec. 2-3).  coef is a HOST array of (M+1) rows of (n-1)^2
  * per-cell values, cell e = cx + cy (n-1): row 0 is the mean coefficient
  * abar_e (defines K_0, Eq. def-stiffness), row k >= 1 is
- * c_k(e) = sqrt(lambda_k) b_k(x_e) (times sigma), defining K_k.  The handle
+ * c_k(e) = sqrt(lambda_k) b_k(x_e) (times sigma), defining K_k.  For elements =
+ * SG_P1 each row holds 2 (n-1)^2 per-triangle values instead, 2e the lower-right and
+ * 2e + 1 the upper-left triangle of cell e (see sg_kl_coef_p1).  The handle
  * copies it.  n = 2^L + 1 with 3 <= n <= 4097; 0 <= M <= 16; 0 <= p <= 10;
- * P <= 4096.  nu1, nu2: damped-Jacobi pre/post smoothing steps of the V-cycle
- * (0 selects 1; at most 4); omega: Jacobi weight (0 selects 8/9). */
+ * P <= 4096.  nu1, nu2: pre/post smoothing steps of the V-cycle (damped Jacobi
+ * for SG_Q1, point Gauss-Seidel sweeps for SG_P1; 0 selects 1; at most 4); omega:
+ * Jacobi weight (0 selects 8/9; unused by SG_P1).  elements: sg_elements (0 = SG_Q1).
+ * gs_order: sg_gs_order of the SG_P1 smoother (ignored by SG_Q1). */
 typedef struct {
   int n;
   int M;
@@ -108,6 +129,8 @@ typedef struct {
   int nu1;
   int nu2;
   double omega;
+  int elements;
+  int gs_order;
 } sg_problem;
 
 /* Solver options (Sec. 4.2, 6).  method: GMRES (right preconditioned) or
@@ -166,6 +189,12 @@ typedef struct {
 int sg_kl_coef(int n, int M, double sigma, double corr_len, const double* abar,
                double* coef_out, double* lambda_out);
 
+/* Host helper for SG_P1 handles (the paper's discretisation, Sec. 6): coef_out ((M+1) x 2 (n-1)^2,
+ * host) with row 0 = 1 and row k = sigma sqrt(lambda_k) b_k at the centroids of the two triangles of
+ * every cell (lower-right at (2/3, 1/3), upper-left at (1/3, 2/3) of the cell), the same modes as
+ * sg_kl_coef.  lambda_out may be NULL.  Pure host computation. */
+int sg_kl_coef_p1(int n, int M, double sigma, double corr_len, double* coef_out, double* lambda_out);
+
 /* Host helper, coercivity check of a coefficient set (Sec. 2.1: the paper's
  * assumption that a stays above a positive constant, and its remark that the
  * truncated expansion can violate it): *amin_out = min over the (n-1)^2 cells of
@@ -192,7 +221,8 @@ int sg_basis(sg_handle h, int* alpha);
 
 /* Load vector of the SG system (Eq. tensor-product's right-hand side): f is
  * deterministic, so only the mean PC block is nonzero, F = e_0 (x) F_0, with the
- * lumped Q1 load F_0[s] = h^2 f_s (h = 1/(n-1); exact for constant f).  f_nodes: the
+ * lumped load F_0[s] = h^2 f_s (h = 1/(n-1); for Q1 exact with constant f, for SG_P1 the lumped
+ * mass of the six triangles around a vertex).  f_nodes: the
  * N_x interior nodal values of f (device, FP64), or NULL for f = 1.  F: device,
  * FP64, P * N_x values, fully overwritten (the blocks i >= 1 are set to zero).
  * Stream-ordered on the handle's stream; returns before the kernel finishes. */

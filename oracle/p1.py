@@ -18,7 +18,10 @@ used here are:
   transpose, coarse operators Galerkin products, the coarsest grid (one interior vertex) solved
   exactly;
 * pre-smoothing is forward lexicographic Gauss-Seidel and post-smoothing backward Gauss-Seidel,
-  which makes the cycle a symmetric operator (PCG with B_D needs a symmetric preconditioner).
+  which makes the cycle a symmetric operator (PCG with B_D needs a symmetric preconditioner);
+  ``order="rb"`` takes the red-black order instead (the multicolour reading of a parallel point
+  Gauss-Seidel): the unknowns of colour (x + y) mod 2 = 0 first, then colour 1, each colour in
+  lexicographic order, and the backward sweep in the reverse of that order.
 
 For B_T the module also has the reading that the paper's counts support best: the 2 x 2 split of
 Eq. hierarchical_structure with the lower-degree block A_hat approximated by one V(2,2) of a point
@@ -132,10 +135,20 @@ def prolongation(nc):
     return sp.csr_matrix((vals, (rows, cols)), shape=(mf * mf, mc * mc))
 
 
-class GSHierarchy:
-    """V(nu1, nu2) cycle with forward Gauss-Seidel pre- and backward Gauss-Seidel post-smoothing."""
+def red_black_order(n):
+    """Permutation of the (n-2)^2 interior vertices of an n-grid (index (x-1) + (y-1)(n-2)): the
+    vertices with (x + y) even in lexicographic order, then those with (x + y) odd."""
+    m = n - 2
+    vx, vy = np.meshgrid(np.arange(1, n - 1), np.arange(1, n - 1))
+    colour = ((vx + vy) % 2).reshape(-1)
+    return np.concatenate([np.nonzero(colour == 0)[0], np.nonzero(colour == 1)[0]])
 
-    def __init__(self, K0, n, nu1=2, nu2=2, coarsest=3):
+
+class GSHierarchy:
+    """V(nu1, nu2) cycle with forward Gauss-Seidel pre- and backward Gauss-Seidel post-smoothing, in
+    lexicographic (``order="lex"``) or red-black (``order="rb"``) order of the unknowns."""
+
+    def __init__(self, K0, n, nu1=2, nu2=2, coarsest=3, order="lex"):
         self.sizes = mg.grid_sizes(n, coarsest)
         self.nu1, self.nu2 = nu1, nu2
         self.A = [sp.csr_matrix(K0)]
@@ -144,10 +157,21 @@ class GSHierarchy:
             Pl = prolongation(self.sizes[l + 1])
             self.P.append(Pl)
             self.A.append((Pl.T @ self.A[l] @ Pl).tocsr())
-        # D + L and D + U as sparse LU factors with the natural order (plain triangular solves)
-        self.low = [spla.splu(sp.tril(A).tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0) for A in self.A[:-1]]
-        self.up = [spla.splu(sp.triu(A).tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0) for A in self.A[:-1]]
+        # the sweep order of each level as a permutation (identity for the lexicographic order)
+        self.perm = [np.arange(A.shape[0]) if order == "lex" else red_black_order(nl)
+                     for A, nl in zip(self.A, self.sizes)]
+        # D + L and D + U of the permuted matrix as sparse LU factors with the natural order (plain
+        # triangular solves): one forward / backward Gauss-Seidel sweep in that order
+        Ap = [A[q][:, q] for A, q in zip(self.A[:-1], self.perm)]
+        self.low = [spla.splu(sp.tril(A).tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0) for A in Ap]
+        self.up = [spla.splu(sp.triu(A).tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0) for A in Ap]
         self.coarse_inv = np.linalg.inv(self.A[-1].toarray())
+
+    def _sweep(self, factor, level, x, b):
+        q = self.perm[level]
+        d = np.zeros_like(x)
+        d[q] = factor.solve((b - self.A[level] @ x)[q])
+        return x + d
 
     def vcycle(self, b, level=0):
         """One cycle from a zero initial guess; b is (N_l,) or (N_l, nrhs)."""
@@ -156,11 +180,11 @@ class GSHierarchy:
             return self.coarse_inv @ b
         x = np.zeros_like(b)
         for _ in range(self.nu1):
-            x = x + self.low[level].solve(b - A @ x)
+            x = self._sweep(self.low[level], level, x, b)
         bc = self.P[level].T @ (b - A @ x)
         x = x + self.P[level] @ self.vcycle(bc, level + 1)
         for _ in range(self.nu2):
-            x = x + self.up[level].solve(b - A @ x)
+            x = self._sweep(self.up[level], level, x, b)
         return x
 
 

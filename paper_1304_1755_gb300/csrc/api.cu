@@ -618,7 +618,8 @@ int precond_blocktri_exact(sg_ctx* h, const double* R, double* Z, int transpose)
   int rc;
   if (h->p == 0) return precond_blocktri(h, SG_F64, R, Z, SG_F64, transpose);
   if (!h->child) {
-    sg_problem pr{h->n, h->M, h->p - 1, h->family, h->coef_h.data(), h->nu1, h->nu2, h->omega};
+    sg_problem pr{h->n, h->M, h->p - 1, h->family, h->coef_h.data(), h->nu1, h->nu2, h->omega, h->elements,
+                  h->gs_order};
     sg_handle c = nullptr;
     if ((rc = sg_setup(&pr, h->stream, &c))) return sg_fail(h, rc, "exact block-triangular: set-up of the degree p-1 "
                                                                      "system failed: " + std::string(sg_last_error(nullptr)));
@@ -666,6 +667,7 @@ void destroy_ctx(sg_ctx* h) {
     h->child = nullptr;
   }
   cudaFree(h->xbuf);
+  cudaFree(h->ew), cudaFree(h->p1w);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
   cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->w64), cudaFree(h->pvec);
@@ -721,6 +723,12 @@ int sg_kl_coef(int n, int M, double sigma, double corr_len, const double* abar, 
   return kl_coef_host(n, M, sigma, corr_len, abar, coef_out, lambda_out);
 }
 
+int sg_kl_coef_p1(int n, int M, double sigma, double corr_len, double* coef_out, double* lambda_out) {
+  if (n < 3 || M < 0 || M > 64 || !coef_out || !(corr_len > 0) || !std::isfinite(sigma))
+    return sg_fail(nullptr, SG_E_ARG, "sg_kl_coef_p1: bad argument");
+  return kl_coef_p1_host(n, M, sigma, corr_len, coef_out, lambda_out);
+}
+
 int sg_min_coef(int n, int M, const double* coef, double xi_max, double* amin_out) {
   if (n < 3 || M < 0 || !coef || !amin_out || !(xi_max >= 0) || !std::isfinite(xi_max))
     return sg_fail(nullptr, SG_E_ARG, "sg_min_coef: bad argument");
@@ -766,6 +774,16 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
   h->Nx = (size_t)h->m * h->m, h->Nc = (size_t)(n - 1) * (n - 1);
   h->nu1 = nu1, h->nu2 = nu2;
   h->omega = prob->omega > 0 ? prob->omega : 8.0 / 9.0;
+  if (prob->elements != SG_Q1 && prob->elements != SG_P1) {
+    delete h;
+    return sg_fail(nullptr, SG_E_ARG, "sg_setup: elements must be SG_Q1 or SG_P1");
+  }
+  h->elements = prob->elements;
+  if (prob->gs_order != SG_GS_LEX && prob->gs_order != SG_GS_RB) {
+    delete h;
+    return sg_fail(nullptr, SG_E_ARG, "sg_setup: gs_order must be SG_GS_LEX or SG_GS_RB");
+  }
+  h->gs_order = prob->gs_order;
   h->stream = (cudaStream_t)stream;
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
@@ -774,11 +792,12 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
   build_basis(M, p, h->alpha, h->lvl_off);
   h->P = h->lvl_off.back();
   h->Np = (h->Nx * (size_t)h->P + 63) / 64 * 64;
-  h->coef_h.assign(prob->coef, prob->coef + (size_t)(M + 1) * h->Nc);
+  const size_t ncoef = (h->elements == SG_P1 ? 2 : 1) * h->Nc;     // per cell, or per triangle (SG_P1)
+  h->coef_h.assign(prob->coef, prob->coef + (size_t)(M + 1) * ncoef);
   for (double v : h->coef_h)
     if (!std::isfinite(v)) { delete h; return sg_fail(nullptr, SG_E_ARG, "sg_setup: non-finite coefficient"); }
   h->const_mean = true;
-  for (size_t e = 0; e < h->Nc; ++e)
+  for (size_t e = 0; e < ncoef; ++e)
     if (h->coef_h[e] != 1.0) { h->const_mean = false; break; }
   int rc;
   std::vector<float> c32(h->coef_h.begin(), h->coef_h.end());
@@ -788,11 +807,13 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
     const df2 d = df_from_double(v);
     cdf.push_back(d.hi), cdf.push_back(d.lo);
   }
+  const bool q1 = h->elements == SG_Q1;
   if ((rc = upload(h, &h->coef64, h->coef_h.data(), h->coef_h.size())) ||
-      (rc = upload(h, &h->coef32, c32.data(), c32.size())) || (rc = upload(h, &h->coefdf, cdf.data(), cdf.size())) ||
+      (q1 && (rc = upload(h, &h->coef32, c32.data(), c32.size()))) ||
+      (q1 && (rc = upload(h, &h->coefdf, cdf.data(), cdf.size()))) ||
       (rc = upload_terms(h, h->t_all, 0)) ||
       (rc = upload_terms(h, h->t_lower, 1)) || (rc = upload_terms(h, h->t_upper, 2)) ||
-      (rc = upload_terms(h, h->t_off, 3)) || (rc = upload_terms(h, h->t_diag, 4)) || (rc = upload_weights(h))) {
+      (rc = upload_terms(h, h->t_off, 3)) || (rc = upload_terms(h, h->t_diag, 4)) || (q1 && (rc = upload_weights(h)))) {
     std::string e = h->err;
     destroy_ctx(h);
     return sg_fail(nullptr, rc, "sg_setup: " + e);
@@ -810,6 +831,15 @@ int sg_setup(const sg_problem* prob, void* stream, sg_handle* out) {
   }
   h->lc = 0;
   while (h->lc < h->nlev && h->lev[h->lc].n > 33) ++h->lc;
+  if (h->elements == SG_P1) {
+    if ((rc = setup_p1(h))) {
+      std::string e = h->err;
+      destroy_ctx(h);
+      return sg_fail(nullptr, rc, "sg_setup: " + e);
+    }
+    *out = h;
+    return SG_OK;
+  }
   if (!h->const_mean) {
     std::vector<std::vector<double>> st;
     galerkin_stencils(n, h->nlev, h->coef_h.data(), st);
@@ -929,6 +959,8 @@ static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve
        o.inner_restart < 0 || o.inner_restart > 32))
     return sg_fail(h, SG_E_ARG, "sg_solve: the exact block-triangular preconditioner needs FGMRES in FP64 "
                                 "(pc_prec SG_F64, arith SG_ARITH_F64) and inner_restart <= 32");
+  if (h->elements == SG_P1 && (o.pc_prec != SG_F64 || o.arith != SG_ARITH_F64))
+    return sg_fail(h, SG_E_ARG, "sg_solve: P1 elements solve in FP64 only (pc_prec SG_F64, arith SG_ARITH_F64)");
   h->inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-12;
   h->inner_restart = o.inner_restart > 0 ? o.inner_restart : 30;
   if (o.arith == SG_ARITH_DF64 && (o.method != SG_FGMRES || o.pc_prec == SG_F64))
@@ -1047,6 +1079,7 @@ int sg_objective(sg_handle h, const double* U, double* J, double* G) {
 
 int sg_adjoint_gradients(sg_handle h, const double* U, const double* Lam, double sigma, double* g_abar, double* g_sigma) {
   if (!h || !U || !Lam) return h ? sg_fail(h, SG_E_ARG, "sg_adjoint_gradients: null argument") : SG_E_ARG;
+  if (h->elements != SG_Q1) return sg_fail(h, SG_E_ARG, "sg_adjoint_gradients: Q1 elements only");
   if (const int rcd = sg_check_device(h, "sg_adjoint_gradients")) return rcd;
   int rc;
   if (g_abar && (rc = adj_cell_forms(h, U, Lam, g_abar))) return rc;

@@ -24,6 +24,7 @@ constexpr int kStrips[] = {4, 8, 16, 32, 64};
 extern "C" int sg_autotune(sg_handle h, int which) {
   if (!h) return SG_E_ARG;
   if (const int rcd = sg_check_device(h, "sg_autotune")) return rcd;
+  if (h->elements != SG_Q1) return SG_OK;                 // the P1 operator has no tile to tune
   if (which == 0) which = 7;
   const auto key = std::make_tuple(h->n, h->M, h->p, h->t_all.nnz, h->const_mean);
   std::lock_guard<std::mutex> lock(g_tune_mu);

@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "df64.cuh"
 #include "sg_internal.h"
 
 namespace {
@@ -157,25 +158,26 @@ __global__ void k_g_update_q(double* __restrict__ U, const float* __restrict__ Z
   const int b = blockIdx.y;
   const int nz = min(d->k - c0, NV);
   if (nz <= 0) return;
-  double c[NV];
+  df2 c[NV];
   float sc[NV], qu[NV];
 #pragma unroll
   for (int l = 0; l < NV; ++l) {
-    c[l] = (l < nz) ? d->y[c0 + l] : 0.0;
+    c[l] = df_from_double((l < nz) ? d->y[c0 + l] : 0.0);
     const unsigned mb = (l < nz) ? qmax[(size_t)(c0 + l) * P + b] : 0u;
     sc[l] = qgrid_scale(mb), qu[l] = qgrid_quantum(mb);
   }
   double* Ub = U + (size_t)b * Nx;
   const float* Zb = Z + (size_t)c0 * ldz + (size_t)b * Nx;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
-    double u = Ub[s];
+    dacc a = dacc_zero();
 #pragma unroll
     for (int l = 0; l < NV; ++l)
       if (l < nz) {
         const float z = Zb[(size_t)l * ldz + s];
-        u += c[l] * (double)__fmul_rn(__fsub_rn(__fmaf_rn(z, sc[l], SG_QBIAS), SG_QBIAS), qu[l]);
+        dacc_fma(a, c[l], __fmul_rn(__fsub_rn(__fmaf_rn(z, sc[l], SG_QBIAS), SG_QBIAS), qu[l]));
       }
-    Ub[s] = u;
+    const df2 r = dacc_get(a);
+    Ub[s] = (Ub[s] + (double)r.hi) + (double)r.lo;
   }
 }
 
@@ -185,16 +187,30 @@ __global__ void k_g_update(double* __restrict__ U, const TZ* __restrict__ Z, siz
                            size_t N) {
   const int nz = min(d->k - c0, NV);
   if (nz <= 0) return;
-  double c[NV];
-#pragma unroll
-  for (int l = 0; l < NV; ++l) c[l] = (l < nz) ? d->y[c0 + l] : 0.0;
   const TZ* Zc = Z + (size_t)c0 * ldz;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    double u = U[i];
+  if constexpr (sizeof(TZ) == 8) {
+    double c[NV];
 #pragma unroll
-    for (int l = 0; l < NV; ++l)
-      if (l < nz) u += c[l] * ld_as<double>(Zc + (size_t)l * ldz + i);
-    U[i] = u;
+    for (int l = 0; l < NV; ++l) c[l] = (l < nz) ? d->y[c0 + l] : 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+      double u = U[i];
+#pragma unroll
+      for (int l = 0; l < NV; ++l)
+        if (l < nz) u += c[l] * ld_as<double>(Zc + (size_t)l * ldz + i);
+      U[i] = u;
+    }
+  } else {                       // as k_update: the sum in double-float, one FP64 addition
+    df2 c[NV];
+#pragma unroll
+    for (int l = 0; l < NV; ++l) c[l] = df_from_double((l < nz) ? d->y[c0 + l] : 0.0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+      dacc a = dacc_zero();
+#pragma unroll
+      for (int l = 0; l < NV; ++l)
+        if (l < nz) dacc_fma(a, c[l], ld_as<float>(Zc + (size_t)l * ldz + i));
+      const df2 r = dacc_get(a);
+      U[i] = (U[i] + (double)r.hi) + (double)r.lo;
+    }
   }
 }
 

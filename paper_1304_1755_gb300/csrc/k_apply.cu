@@ -492,6 +492,9 @@ __global__ void __launch_bounds__(NT, 4) k_apply_f32x2(ApplyArgs a) {
   const bool cellA = cx0 <= n - 2, cellB = cx0 + 1 <= n - 2;   // cells inside the grid of cells
   const bool outA = lane >= 1 && ok0, outB = lane <= 30 && ok1;   // nodes cx0, cx0 + 1 finished here
   const int cxw = min(cx0, n - 3);                             // weight pair (cells n - 3, n - 2 at most; n - 3 is even)
+  // all lanes' node columns cx0, cx0 + 1 interior (first cell 62 w >= 1, last 62 w + 63 <= n - 2): uniform per warp
+  const int wx0 = cx0 - 2 * lane;
+  const bool inner = wx0 >= 1 && wx0 + 63 <= n - 2;
   const bool wshift = cxw != cx0;                              // only past the last cell pair (weights unused)
   float AAp = 0.f, BAp = 0.f, CAp = 0.f, ABp = 0.f, BBp = 0.f, CBp = 0.f;   // previous cell row's features
   typename E::Raw rvA{}, rvB{};
@@ -506,17 +509,33 @@ __global__ void __launch_bounds__(NT, 4) k_apply_f32x2(ApplyArgs a) {
     const int e = cxw + cy * (n - 1);
     float a0 = 0.f, b0 = 0.f, c0 = 0.f, d0 = 0.f;              // cell A corners mixed
     float a1 = 0.f, b1 = 0.f, c1 = 0.f, d1 = 0.f;              // cell B
+    if (inner && lo_ok && hi_ok) {
+      // every lane's corners are interior nodes in this cell row: no predicates, no selects
 #pragma unroll 4
-    for (int t = 0; t < nt; ++t) {
-      const XE* p = xp[t] + sA;
-      const float2 cw = __ldg(reinterpret_cast<const float2*>(wp[t] + e));
-      const float g = gg[t];
-      const float wA = (wshift ? cw.y : cw.x) * g, wB = cw.y * g;
-      const float z0b = LX::ldq(p, 0, ok0 && lo_ok), z1b = LX::ldq(p + 1, 0, ok1 && lo_ok);
-      const float z0t = LX::ldq(p + m, 0, ok0 && hi_ok), z1t = LX::ldq(p + m + 1, 0, ok1 && hi_ok);
-      const float z2b = __shfl_down_sync(0xffffffffu, z0b, 1), z2t = __shfl_down_sync(0xffffffffu, z0t, 1);
-      a0 = fmaf(wA, z0b, a0), b0 = fmaf(wA, z1b, b0), c0 = fmaf(wA, z1t, c0), d0 = fmaf(wA, z0t, d0);
-      a1 = fmaf(wB, z1b, a1), b1 = fmaf(wB, z2b, b1), c1 = fmaf(wB, z2t, c1), d1 = fmaf(wB, z1t, d1);
+      for (int t = 0; t < nt; ++t) {
+        const XE* p = xp[t] + sA;
+        const float2 cw = __ldg(reinterpret_cast<const float2*>(wp[t] + e));
+        const float g = gg[t];
+        const float wA = cw.x * g, wB = cw.y * g;
+        const float z0b = LX::ldq(p, 0, true), z1b = LX::ldq(p + 1, 0, true);
+        const float z0t = LX::ldq(p + m, 0, true), z1t = LX::ldq(p + m + 1, 0, true);
+        const float z2b = __shfl_down_sync(0xffffffffu, z0b, 1), z2t = __shfl_down_sync(0xffffffffu, z0t, 1);
+        a0 = fmaf(wA, z0b, a0), b0 = fmaf(wA, z1b, b0), c0 = fmaf(wA, z1t, c0), d0 = fmaf(wA, z0t, d0);
+        a1 = fmaf(wB, z1b, a1), b1 = fmaf(wB, z2b, b1), c1 = fmaf(wB, z2t, c1), d1 = fmaf(wB, z1t, d1);
+      }
+    } else {
+#pragma unroll 4
+      for (int t = 0; t < nt; ++t) {
+        const XE* p = xp[t] + sA;
+        const float2 cw = __ldg(reinterpret_cast<const float2*>(wp[t] + e));
+        const float g = gg[t];
+        const float wA = (wshift ? cw.y : cw.x) * g, wB = cw.y * g;
+        const float z0b = LX::ldq(p, 0, ok0 && lo_ok), z1b = LX::ldq(p + 1, 0, ok1 && lo_ok);
+        const float z0t = LX::ldq(p + m, 0, ok0 && hi_ok), z1t = LX::ldq(p + m + 1, 0, ok1 && hi_ok);
+        const float z2b = __shfl_down_sync(0xffffffffu, z0b, 1), z2t = __shfl_down_sync(0xffffffffu, z0t, 1);
+        a0 = fmaf(wA, z0b, a0), b0 = fmaf(wA, z1b, b0), c0 = fmaf(wA, z1t, c0), d0 = fmaf(wA, z0t, d0);
+        a1 = fmaf(wB, z1b, a1), b1 = fmaf(wB, z2b, b1), c1 = fmaf(wB, z2t, c1), d1 = fmaf(wB, z1t, d1);
+      }
     }
     // features; cells outside the grid of cells carry none
     float AA = cellA ? 0.5f * (a0 - c0) : 0.f, BA = cellA ? 0.5f * (b0 - d0) : 0.f;
@@ -619,6 +638,8 @@ int pick_x(sg_ctx* h, ApplyArgs& a, int xprec, int yprec, int rprec) {
 
 int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int yprec, void* Y, size_t ylo,
                  int rprec, const void* R, size_t rlo, int row0, int nrows, int ybase, int rbase, int arith) {
+  if (h->elements == SG_P1)
+    return launch_apply_p1(h, which, xprec, X, yprec, Y, rprec, R, row0, nrows, ybase, rbase, arith);
   if (nrows <= 0) return SG_OK;
   const TermTable& T = which == 0   ? h->t_all
                        : which == 1 ? h->t_lower

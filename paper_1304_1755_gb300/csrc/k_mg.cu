@@ -286,7 +286,7 @@ int ensure_prec_work(sg_ctx* h, int mode) {
   int nqmax = 0;
   for (int q = 0; q <= h->p; ++q) nqmax = std::max(nqmax, h->lvl_off[q + 1] - h->lvl_off[q]);
   if (!(W.T = sg_galloc(es * (size_t)nqmax * h->Nx))) return sg_fail(h, SG_E_ALLOC, "alloc stage buffer");
-  for (int l = 1; l < h->nlev; ++l) {
+  for (int l = 1; l < (h->elements == SG_P1 ? 1 : h->nlev); ++l) {   // the P1 cycle keeps its own levels
     const size_t bytes = es * (size_t)h->P * h->lev[l].N;
     if (!(W.b[l] = sg_galloc(bytes)) || !(W.x[l] = sg_galloc(bytes)))
       return sg_fail(h, SG_E_ALLOC, "alloc multigrid level");
@@ -298,6 +298,10 @@ int ensure_prec_work(sg_ctx* h, int mode) {
 int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard) {
   if (nb <= 0) return SG_OK;
   if (nb > h->P) return sg_fail(h, SG_E_ARG, "vcycle: more blocks than the workspace holds");
+  if (h->elements == SG_P1) {
+    if (prec != SG_F64 || bprec != SG_F64) return sg_fail(h, SG_E_ARG, "P1 elements: FP64 V-cycles only");
+    return vcycle_p1(h, nb, (const double*)B, h->Nx, (double*)X, h->Nx);
+  }
   int rc = ensure_prec_work(h, prec);
   if (rc) return rc;
   PrecWork& W = h->work[wprec_of(prec)];
@@ -472,6 +476,7 @@ extern "C" int sg_vcycle_static(sg_handle h, const double* B, void* X, int nbloc
   if (!h || !B || !X || prec < 0 || prec > 2 || nblocks < 0 || nblocks > h->P)
     return h ? sg_fail(h, SG_E_ARG, "sg_vcycle_static: bad argument") : SG_E_ARG;
   if (const int rcd = sg_check_device(h, "sg_vcycle_static")) return rcd;   // the array's address is per device
+  if (h->elements != SG_Q1) return sg_fail(h, SG_E_ARG, "sg_vcycle_static: Q1 elements only");
   if (nblocks == 0) return SG_OK;
   const size_t need = static_scratch_bytes(h, nblocks, prec);
   if (need > VCYCLE_SCRATCH_BYTES)

@@ -238,15 +238,30 @@ __global__ void k_df_to_f64(const float* __restrict__ x, double* __restrict__ y,
 template <typename TZ, int NV>
 __global__ void k_update(double* __restrict__ U, const TZ* __restrict__ Z, size_t ldz, int nz,
                          const double* __restrict__ y, size_t N) {
-  double c[NV];
+  if constexpr (sizeof(TZ) == 8) {
+    double c[NV];
 #pragma unroll
-  for (int l = 0; l < NV; ++l) c[l] = (l < nz) ? y[l] : 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    double u = U[i];
+    for (int l = 0; l < NV; ++l) c[l] = (l < nz) ? y[l] : 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+      double u = U[i];
 #pragma unroll
-    for (int l = 0; l < NV; ++l)
-      if (l < nz) u += c[l] * ld_as<double>(Z + (size_t)l * ldz + i);
-    U[i] = u;
+      for (int l = 0; l < NV; ++l)
+        if (l < nz) u += c[l] * ld_as<double>(Z + (size_t)l * ldz + i);
+      U[i] = u;
+    }
+  } else {
+    // FP32 / BF16 z: the sum over l in double-float (FP32 instructions), added to U in FP64 once
+    df2 c[NV];
+#pragma unroll
+    for (int l = 0; l < NV; ++l) c[l] = df_from_double((l < nz) ? y[l] : 0.0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+      dacc a = dacc_zero();
+#pragma unroll
+      for (int l = 0; l < NV; ++l)
+        if (l < nz) dacc_fma(a, c[l], ld_as<float>(Z + (size_t)l * ldz + i));
+      const df2 r = dacc_get(a);
+      U[i] = (U[i] + (double)r.hi) + (double)r.lo;
+    }
   }
 }
 
@@ -480,15 +495,22 @@ int vec_fill(sg_ctx* h, double* y, size_t N, double v) {
 __global__ void k_block_absmax(const float* __restrict__ Z, size_t Nx, unsigned* __restrict__ qmax) {
   const float* z = Z + (size_t)blockIdx.y * Nx;
   unsigned m = 0;
-  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x)
-    m = max(m, __float_as_uint(fabsf(z[s])));
+  const size_t st = (size_t)gridDim.x * blockDim.x;
+  size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; s + 3 * st < Nx; s += 4 * st) {                      // four independent loads in flight
+    const float a = __ldg(z + s), b = __ldg(z + s + st), c = __ldg(z + s + 2 * st), d = __ldg(z + s + 3 * st);
+    m = max(max(m, __float_as_uint(fabsf(a))), max(__float_as_uint(fabsf(b)),
+                                                    max(__float_as_uint(fabsf(c)), __float_as_uint(fabsf(d)))));
+  }
+  for (; s < Nx; s += st) m = max(m, __float_as_uint(fabsf(z[s])));
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m) atomicMax(qmax + blockIdx.y, m);
 }
 
 int block_absmax(sg_ctx* h, const float* Z, unsigned* qmax) {
   SG_CUDA(h, cudaMemsetAsync(qmax, 0, sizeof(unsigned) * h->P, h->stream));
-  const int gx = (int)std::max<size_t>(1, std::min<size_t>((h->Nx + 4095) / 4096, 64));
+  // about eight warps per SM per block row of the grid, each thread with 16 or more values
+  const int gx = (int)std::max<size_t>(1, std::min<size_t>((h->Nx + 4095) / 4096, (size_t)(152 * 8 + h->P - 1) / h->P));
   k_block_absmax<<<dim3(gx, h->P), 256, 0, h->stream>>>(Z, h->Nx, qmax);
   SG_CUDA(h, cudaGetLastError());
   count_launch(h);
@@ -501,27 +523,30 @@ __device__ __forceinline__ float qgrid_value(float z, float s, float q) {
   return __fmul_rn(__fsub_rn(__fmaf_rn(z, s, SG_QBIAS), SG_QBIAS), q);
 }
 
-// FP64 U += sum_l y_l z'_l; grid x over the nodes of a block, grid y over the blocks
+// FP64 U += sum_l y_l z'_l; grid x over the nodes of a block, grid y over the blocks.  The sum over l is
+// accumulated in double-float from the exact FP32 grid values (FP32 instructions; an FP64 multiply-add per
+// term would make this pass FP64-bound on GB300) and added to U in FP64 once.
 template <int NV>
 __global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, size_t ldz, int nz,
                            const double* __restrict__ y, size_t Nx, const unsigned* __restrict__ qmax, int P) {
   const int b = blockIdx.y;
-  double c[NV];
+  df2 c[NV];
   float sc[NV], qu[NV];
 #pragma unroll
   for (int l = 0; l < NV; ++l) {
-    c[l] = (l < nz) ? y[l] : 0.0;
+    c[l] = df_from_double((l < nz) ? y[l] : 0.0);
     const unsigned mb = (l < nz) ? qmax[(size_t)l * P + b] : 0u;
     sc[l] = qgrid_scale(mb), qu[l] = qgrid_quantum(mb);
   }
   double* Ub = U + (size_t)b * Nx;
   const float* Zb = Z + (size_t)b * Nx;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
-    double u = Ub[s];
+    dacc a = dacc_zero();
 #pragma unroll
     for (int l = 0; l < NV; ++l)
-      if (l < nz) u += c[l] * (double)qgrid_value(Zb[(size_t)l * ldz + s], sc[l], qu[l]);
-    Ub[s] = u;
+      if (l < nz) dacc_fma(a, c[l], qgrid_value(Zb[(size_t)l * ldz + s], sc[l], qu[l]));
+    const df2 r = dacc_get(a);
+    Ub[s] = (Ub[s] + (double)r.hi) + (double)r.lo;
   }
 }
 

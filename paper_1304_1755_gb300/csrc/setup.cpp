@@ -51,6 +51,41 @@ double eval_1d(const Mode1D& md, double y) {
 }
 }  // namespace
 
+// The same modes at the centroids of the two right triangles of every cell (the paper's P1
+// discretisation): entry 2e at (cx + 2/3, cy + 1/3) h, entry 2e + 1 at (cx + 1/3, cy + 2/3) h.
+int kl_coef_p1_host(int n, int M, double sigma, double corr_len, double* coef, double* lam) {
+  if (n < 3 || M < 0 || M > 64 || !coef || !(corr_len > 0)) return SG_E_ARG;
+  const int nc1 = n - 1;
+  const size_t Nt = 2 * (size_t)nc1 * nc1;
+  std::vector<Mode1D> m1 = kl_1d(M + 1, corr_len);
+  struct P2 { double lam; int i, j; };
+  std::vector<P2> pairs;
+  for (int i = 0; i <= M; ++i)
+    for (int j = 0; j <= M; ++j) pairs.push_back({m1[i].lam * m1[j].lam, i, j});
+  std::stable_sort(pairs.begin(), pairs.end(), [](const P2& x, const P2& y) {
+    if (x.lam != y.lam) return x.lam > y.lam;
+    return x.i < y.i;
+  });
+  for (size_t e = 0; e < Nt; ++e) coef[e] = 1.0;
+  const double h = 1.0 / nc1;
+  const double off[2][2] = {{2.0 / 3.0, 1.0 / 3.0}, {1.0 / 3.0, 2.0 / 3.0}};   // (x, y) in the cell, per triangle
+  for (int k = 1; k <= M; ++k) {
+    const P2& pr = pairs[k - 1];
+    if (lam) lam[k - 1] = pr.lam;
+    const double s = sigma * std::sqrt(pr.lam);
+    double* row = coef + (size_t)k * Nt;
+    for (int tri = 0; tri < 2; ++tri)
+      for (int cy = 0; cy < nc1; ++cy) {
+        const double by = eval_1d(m1[pr.j], cy * h - 0.5 + off[tri][1] * h);
+        for (int cx = 0; cx < nc1; ++cx) {
+          const double bx = eval_1d(m1[pr.i], cx * h - 0.5 + off[tri][0] * h);
+          row[2 * ((size_t)cy * nc1 + cx) + tri] = s * bx * by;
+        }
+      }
+  }
+  return SG_OK;
+}
+
 int kl_coef_host(int n, int M, double sigma, double corr_len, const double* abar, double* coef, double* lam) {
   if (n < 3 || M < 0 || M > 64 || !coef || !(corr_len > 0)) return SG_E_ARG;
   const int nc1 = n - 1;

@@ -98,6 +98,11 @@ struct sg_ctx {
   int nu1 = 1, nu2 = 1;
   double omega = 8.0 / 9.0;
   bool const_mean = true;
+  int elements = SG_Q1;                 // SG_Q1 or SG_P1 (the paper's triangles, point Gauss-Seidel cycle)
+  int gs_order = SG_GS_LEX;             // SG_P1 smoother order (lexicographic or red-black)
+  double* ew = nullptr;                 // SG_P1: edge weights per mode, (M+1) x 2 x n^2 (horizontal, vertical)
+  double* p1w = nullptr;                // SG_P1: V-cycle workspace, P x p1w_ld doubles
+  size_t p1w_ld = 0;
   int device = -1;                      // the CUDA device the handle was set up on
   cudaStream_t stream = nullptr;
   std::vector<int> alpha;               // P * M
@@ -206,6 +211,7 @@ inline int wprec_of(int mode) { return mode == SG_BF16Z ? SG_BF16 : mode; }
 
 // setup.cpp
 int kl_coef_host(int n, int M, double sigma, double corr_len, const double* abar, double* coef, double* lam);
+int kl_coef_p1_host(int n, int M, double sigma, double corr_len, double* coef, double* lam);
 void build_basis(int M, int p, std::vector<int>& alpha, std::vector<int>& lvl_off);
 double gamma_1d(int family, int nn);
 void build_terms(const sg_ctx* h, int which, std::vector<int>& row_ptr, std::vector<int>& tj,
@@ -225,6 +231,13 @@ int ensure_krylov_ext(sg_ctx* h, int nv, int nz, int zprec, int layout);
 // array at offset *lo (elements).  arith: SG_F64, SG_F32 or SG_DF64.
 int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int yprec, void* Y, size_t ylo,
                  int rprec, const void* R, size_t rlo, int row0, int nrows, int ybase, int rbase, int arith);
+
+// k_p1.cu (SG_P1 handles): the operator (FP64; same arguments as launch_apply) and the point
+// Gauss-Seidel V-cycle (FP64 B with leading dimension ldb, FP64 X with ldx)
+int launch_apply_p1(sg_ctx* h, int which, int xprec, const void* X, int yprec, void* Y, int rprec, const void* R,
+                    int row0, int nrows, int ybase, int rbase, int arith);
+int vcycle_p1(sg_ctx* h, int nb, const double* B, size_t ldb, double* X, size_t ldx);
+int setup_p1(sg_ctx* h);
 
 // k_mg.cu
 // bguard: B lies in a guarded buffer (sg_galloc), so the tile loaders may over-fetch around it

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libsg.so")
 F64, F32, BF16, DF64, BF16Z = 0, 1, 2, 3, 4   # BF16Z: BF16 preconditioner storage, FP32 output
 ARITH_F64, ARITH_DF64, ARITH_F64_DFOP = 0, 1, 2   # see sg_arith in include/sg.h
 LEGENDRE, HERMITE = 0, 1
+Q1, P1 = 0, 1                                   # sg_elements
+GS_LEX, GS_RB = 0, 1                            # sg_gs_order (P1 smoother)
 GMRES, FGMRES, GPCG, PCG, BGS = 0, 1, 2, 3, 4
 PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM, PC_BLOCKTRI_EXACT = 0, 1, 2, 3, 4
 
@@ -31,7 +33,7 @@ class SGError(RuntimeError):
 class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("M", ctypes.c_int), ("p", ctypes.c_int), ("family", ctypes.c_int),
                 ("coef", ctypes.POINTER(ctypes.c_double)), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("omega", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("elements", ctypes.c_int), ("gs_order", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -55,6 +57,7 @@ VP, DP, IP = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ct
 # exported name -> (restype, argtypes)
 SIGNATURES = {
     "sg_kl_coef": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, VP, VP, VP]),
+    "sg_kl_coef_p1": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, VP, VP]),
     "sg_min_coef": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, VP, ctypes.c_double, DP]),
     "sg_setup": (ctypes.c_int, [ctypes.POINTER(Problem), VP, ctypes.POINTER(VP)]),
     "sg_rhs": (ctypes.c_int, [VP, VP, VP]),
@@ -129,6 +132,15 @@ def sg_kl_coef(n, M, sigma, corr_len=1.0, abar=None):
     return coef, lam[:M]
 
 
+def sg_kl_coef_p1(n, M, sigma, corr_len=1.0):
+    """Host KL helper for P1 elements: ((M+1, 2 (n-1)^2) per-triangle coefficients, lambda[M])."""
+    import numpy as np
+    coef = np.zeros((M + 1, 2 * (n - 1) ** 2))
+    lam = np.zeros(max(M, 1))
+    _check(lib().sg_kl_coef_p1(n, M, sigma, corr_len, _ptr(coef), _ptr(lam)))
+    return coef, lam[:M]
+
+
 def sg_min_coef(coef, n, M, xi_max=3.0 ** 0.5):
     """Host coercivity check: min over cells and over the box |xi_k| <= xi_max of a(x_e, xi)."""
     import numpy as np
@@ -142,11 +154,11 @@ def sg_min_coef(coef, n, M, xi_max=3.0 ** 0.5):
 class Handle:
     """Owns one sg_handle.  Pointer arguments: torch tensors, numpy arrays or ints."""
 
-    def __init__(self, n, M, p, family, coef, nu1=1, nu2=1, omega=0.0, stream=None):
+    def __init__(self, n, M, p, family, coef, nu1=1, nu2=1, omega=0.0, stream=None, elements=0, gs_order=0):
         import numpy as np
         self._coef = np.ascontiguousarray(coef, dtype=np.float64)
-        assert self._coef.shape == (M + 1, (n - 1) ** 2)
-        prob = Problem(n, M, p, family, self._coef.ctypes.data_as(DP), nu1, nu2, omega)
+        assert self._coef.shape == (M + 1, (2 if elements == P1 else 1) * (n - 1) ** 2)
+        prob = Problem(n, M, p, family, self._coef.ctypes.data_as(DP), nu1, nu2, omega, elements, gs_order)
         h = VP()
         s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
         _check(lib().sg_setup(ctypes.byref(prob), s, ctypes.byref(h)))
@@ -267,13 +279,13 @@ def solve_batch(handles, Fs, Us, nstreams=8, method=FGMRES, precond=PC_BLOCKTRI,
 
 
 def solve_batch_graph(handles, Fs, Us, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8,
-                      pc_prec=F64, transpose=False, arith=ARITH_F64, check=True):
+                      pc_prec=F64, transpose=False, arith=ARITH_F64, reorth=0, check=True):
     """sg_solve_batch_graph: the batch solved in one CUDA graph (device-side Arnoldi control, one launch
     per restart cycle of all systems); returns one SolveInfo per system."""
     n = len(handles)
     if len(Fs) != n or len(Us) != n:
         raise ValueError("handles, Fs and Us must have the same length")
-    o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, 0, arith, 0.0, 0)
+    o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, reorth, arith, 0.0, 0)
     hs = (VP * n)(*[h.h for h in handles])
     fp = (VP * n)(*[_ptr(F) for F in Fs])
     up = (VP * n)(*[_ptr(U) for U in Us])
@@ -291,13 +303,13 @@ class Batch:
     launched for every solve (the handles, F and U fixed at creation)."""
 
     def __init__(self, handles, Fs, Us, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8,
-                 pc_prec=F64, transpose=False, arith=ARITH_F64):
+                 pc_prec=F64, transpose=False, arith=ARITH_F64, reorth=0):
         n = len(handles)
         if len(Fs) != n or len(Us) != n:
             raise ValueError("handles, Fs and Us must have the same length")
         self.handles, self.n = handles, n
         self._keep = (Fs, Us)
-        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, 0, arith, 0.0, 0)
+        o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), 0, reorth, arith, 0.0, 0)
         hs = (VP * n)(*[h.h for h in handles])
         fp = (VP * n)(*[_ptr(F) for F in Fs])
         up = (VP * n)(*[_ptr(U) for U in Us])

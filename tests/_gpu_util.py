@@ -66,3 +66,14 @@ def pair(n, M, p, family=basis.LEGENDRE, sigma=0.3, mean="one", nu=(1, 1), seed=
     if key not in _PAIRS:
         _PAIRS[key] = Pair(n, M, p, family, sigma=sigma, mean=mean, nu=nu, seed=seed)
     return _PAIRS[key]
+
+
+def residual_rounding(sys, U, F):
+    """One rounding unit of the relative residual ||F - A U|| / ||F|| in FP64: eps ||(|F| + |A| |U|)|| /
+    ||F||, |A| = sum_k |G_k| (x) |K_k|.  Each entry of a computed F - A U is off by a few eps times the
+    entry of |F| + |A| |U| with signs that mostly cancel over the vector, so two evaluations that sum in
+    different orders (the library's kernels, scipy) differ by a fraction of this unit; near the solve's
+    attainable accuracy the residual itself is of that size."""
+    import dataclasses
+    absys = dataclasses.replace(sys, G=[np.abs(g) for g in sys.G], K=[abs(k) for k in sys.K])
+    return np.finfo(float).eps * np.linalg.norm(np.abs(F) + osg.apply(absys, np.abs(U))) / np.linalg.norm(F)

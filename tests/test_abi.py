@@ -114,6 +114,17 @@ def test_library_kl_helper_matches_oracle(lib, n, M, sigma):
     assert np.array_equal(coef2[0], ab)
 
 
+@pytest.mark.parametrize("n,M,sigma", [(9, 2, 0.3), (33, 4, 0.5), (65, 6, 0.2), (5, 0, 0.1)])
+def test_library_triangle_kl_helper_matches_oracle(lib, n, M, sigma):
+    """sg_kl_coef_p1 (host): the per-triangle coefficients at the centroids, the oracle's."""
+    from oracle import kl, p1
+    from paper_1304_1755_gb300 import sg
+    coef, lam = sg.sg_kl_coef_p1(n, M, sigma)
+    assert coef.shape == (M + 1, 2 * (n - 1) ** 2)
+    assert np.allclose(coef, p1.triangle_coefficients(n, M, sigma), rtol=0, atol=1e-14)
+    assert np.allclose(lam, kl.kl_eigenvalues(M), rtol=1e-13)
+
+
 @pytest.mark.parametrize("n,M,sigma,xi", [(9, 2, 0.3, 3 ** 0.5), (33, 4, 0.5, 3 ** 0.5), (17, 6, 0.2, 2.5)])
 def test_library_coercivity_helper_matches_oracle(lib, n, M, sigma, xi):
     """sg_min_coef (host) against the oracle's corner minimum, itself pinned by enumeration."""

@@ -1,0 +1,161 @@
+"""The paper's own discretisation on the GPU (Sec. 6: linear triangles, point Gauss-Seidel V-cycles)
+against the oracle's version of it (``oracle.p1``): the SG operator, the V-cycle in lexicographic and
+red-black order, the block preconditioners, and the five methods' iteration counts and solutions."""
+import numpy as np
+import pytest
+
+from oracle import basis, krylov, p1, precond, sg as osg
+from paper_1304_1755_gb300 import inputs, sg
+from _gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+ORDERS = {sg.GS_LEX: "lex", sg.GS_RB: "rb"}
+
+
+class P1Pair:
+    def __init__(self, n, M, p, sigma, order=sg.GS_LEX, nu=(2, 2)):
+        import torch
+        self.sys = p1.build(n, M, p, basis.LEGENDRE, sigma)
+        self.h = sg.Handle(n, M, p, sg.LEGENDRE, self.sys.coef, nu1=nu[0], nu2=nu[1], elements=sg.P1,
+                           gs_order=order, stream=torch.cuda.current_stream())
+        assert self.h.P == self.sys.P and self.h.Nx == self.sys.Nx
+        self.hier = p1.GSHierarchy(self.sys.K[0], n, nu1=nu[0], nu2=nu[1], order=ORDERS[order])
+        self.solver = precond.DiagSolver(self.sys.K[0], self.hier)
+        self.N = self.sys.P * self.sys.Nx
+
+
+_PAIRS = {}
+
+
+def pair(*key):
+    if key not in _PAIRS:
+        _PAIRS[key] = P1Pair(*key)
+    return _PAIRS[key]
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,M,p", [(17, 3, 2), (65, 4, 3), (129, 6, 2)])
+def test_operator_matches_oracle(n, M, p):
+    """Y = sum_k (G_k (x) K_k) X with the per-triangle K_k, element by element."""
+    pr = pair(n, M, p, 0.3)
+    X = inputs.uniform(11, pr.N)
+    Y = dev(np.zeros(pr.N))
+    pr.h.apply(dev(X), Y)
+    assert _rel(host(Y), osg.apply(pr.sys, X)) <= 1e-13
+
+
+@pytest.mark.parametrize("order", [sg.GS_LEX, sg.GS_RB])
+@pytest.mark.parametrize("n,nu", [(17, (2, 2)), (65, (2, 2)), (129, (1, 1)), (257, (2, 1))])
+def test_vcycle_matches_oracle(order, n, nu):
+    """One V-cycle from a zero guess on three blocks, every level and sweep order as the oracle's."""
+    pr = pair(n, 1, 1, 0.2, order, nu)
+    Nx = pr.sys.Nx
+    B = inputs.uniform(5, 3 * Nx).reshape(3, Nx)
+    X = dev(np.zeros(3 * Nx))
+    pr.h.vcycle(dev(B.reshape(-1)), X, 3)
+    want = pr.hier.vcycle(B.T).T
+    assert _rel(host(X).reshape(3, Nx), want) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [sg.GS_LEX, sg.GS_RB])
+def test_block_preconditioners_match_oracle(order):
+    """B_T (and its transpose), B_D and B_S applications with the P1 cycle on every diagonal block."""
+    pr = pair(33, 4, 3, 0.3, order)
+    R = inputs.uniform(9, pr.N)
+    Rd = dev(R)
+    cases = (
+        (lambda Z: pr.h.precond_blocktri(Rd, Z), lambda: precond.block_tri_inv(pr.sys, pr.solver, R)),
+        (lambda Z: pr.h.precond_blocktri(Rd, Z, transpose=True),
+         lambda: precond.block_tri_inv(pr.sys, pr.solver, R, transpose=True)),
+        (lambda Z: pr.h.precond_blockdiag(Rd, Z), lambda: precond.block_diag_inv(pr.sys, pr.solver, R)),
+        (lambda Z: pr.h.precond_blocksym(Rd, Z), lambda: precond.block_sym_inv(pr.sys, pr.solver, R)),
+    )
+    for gpu, ora in cases:
+        Z = dev(np.zeros(pr.N))
+        gpu(Z)
+        assert _rel(host(Z), ora()) <= 1e-12
+
+
+METHODS = {  # name: (sg method, sg precond, oracle run)
+    "BT-GMRes": (sg.GMRES, sg.PC_BLOCKTRI,
+                 lambda A, pr, F: krylov.gmres(A, lambda r: precond.block_tri_inv(pr.sys, pr.solver, r), F,
+                                               tol=1e-10, restart=10, maxit=400)),
+    "BT-GPCG": (sg.GPCG, sg.PC_BLOCKTRI,
+                lambda A, pr, F: krylov.gpcg1(A, lambda r: precond.block_tri_inv(pr.sys, pr.solver, r), F,
+                                              tol=1e-10, maxit=400)),
+    "BD-PCG": (sg.PCG, sg.PC_BLOCKDIAG,
+               lambda A, pr, F: krylov.pcg(A, lambda r: precond.block_diag_inv(pr.sys, pr.solver, r), F,
+                                           tol=1e-10, maxit=400)),
+    "BS-PCG": (sg.PCG, sg.PC_BLOCKSYM,
+               lambda A, pr, F: krylov.pcg(A, lambda r: precond.block_sym_inv(pr.sys, pr.solver, r), F,
+                                           tol=1e-10, maxit=400)),
+    "Block-GS": (sg.BGS, sg.PC_BLOCKTRI,
+                 lambda A, pr, F: krylov.block_gauss_seidel(A, lambda r: precond.block_tri_inv(pr.sys, pr.solver, r),
+                                                            F, tol=1e-10, maxit=400)),
+}
+
+
+@pytest.mark.parametrize("order", [sg.GS_LEX, sg.GS_RB])
+@pytest.mark.parametrize("sigma", [0.1, 0.3])
+def test_methods_match_oracle_iterations_and_solution(order, sigma):
+    """The paper's test problem (f = 2 (0.5 - x^2 - y^2), GMRes(10), relative residual 1e-10) at
+    h = 1/32, m = 4, p = 3: each method takes the oracle's iteration count (to within one: both stop
+    on a residual that crosses 1e-10 in the same step unless it lands within rounding of the bar) and
+    reaches the oracle's direct solution."""
+    import torch
+    pr = pair(33, 4, 3, sigma, order)
+    F = p1.rhs(pr.sys)
+    Ustar = osg.solve_direct(osg.assemble(pr.sys), F)
+    A = lambda v: osg.apply(pr.sys, v)
+    for name, (method, pc, run) in METHODS.items():
+        _, its, _ = run(A, pr, F)
+        U = dev(np.zeros(pr.N))
+        info = pr.h.solve(dev(F), U, method=method, precond=pc, restart=10, maxit=400, tol=1e-10,
+                          pc_prec=sg.F64, arith=sg.ARITH_F64)
+        torch.cuda.synchronize()
+        assert info.status == 0 and info.relres_true <= 1.01e-10, (name, info.relres_true)
+        assert abs(info.iters - its) <= 1, (name, info.iters, its)
+        assert np.linalg.norm(host(U) - Ustar) <= 1e-8 * np.linalg.norm(Ustar), name
+
+
+def test_library_rhs_and_kl_coefficients_for_triangles():
+    """sg_kl_coef_p1 gives the oracle's per-triangle coefficients; sg_rhs with the nodal f values
+    gives the lumped load e_0 (x) h^2 f."""
+    n, M = 33, 4
+    coef, _ = sg.sg_kl_coef_p1(n, M, 0.3)
+    assert _rel(coef, p1.triangle_coefficients(n, M, 0.3)) <= 1e-14
+    pr = pair(33, 4, 3, 0.3)
+    h = 1.0 / (n - 1)
+    xs = np.arange(1, n - 1) * h - 0.5
+    Xg, Yg = np.meshgrid(xs, xs)
+    f = (2.0 * (0.5 - Xg ** 2 - Yg ** 2)).reshape(-1)
+    F = dev(np.zeros(pr.N))
+    pr.h.rhs(F, dev(f))
+    assert _rel(host(F), p1.rhs(pr.sys)) <= 1e-15
+
+
+def test_rejects_unsupported_forms():
+    """P1 handles are FP64 only and need the mean coefficient 1; the Q1-only entry points refuse them."""
+    import torch
+    pr = pair(17, 3, 2, 0.3)
+    X = dev(np.zeros(pr.N))
+    with pytest.raises(sg.SGError):
+        pr.h.apply(X.float(), torch.empty_like(X.float()), sg.F32)
+    with pytest.raises(sg.SGError):
+        pr.h.precond_blocktri(X, torch.empty_like(X.float()), sg.F32)
+    with pytest.raises(sg.SGError):
+        pr.h.solve(X, torch.zeros_like(X), pc_prec=sg.F32)
+    with pytest.raises(sg.SGError):
+        pr.h.solve(X, torch.zeros_like(X), arith=sg.ARITH_F64_DFOP)
+    with pytest.raises(sg.SGError):
+        pr.h.vcycle_static(X, torch.empty_like(X), 1)
+    coef = pr.sys.coef.copy()
+    coef[0, 5] = 1.5
+    with pytest.raises(sg.SGError):
+        sg.Handle(17, 3, 2, sg.LEGENDRE, coef, elements=sg.P1)
+    with pytest.raises(sg.SGError):
+        sg.Handle(17, 3, 2, sg.LEGENDRE, pr.sys.coef, elements=sg.P1, gs_order=2)

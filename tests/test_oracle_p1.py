@@ -232,3 +232,41 @@ def test_four_colour_order_has_no_coupling_inside_a_colour():
     N = cyc.A[0].shape[0]
     B = cyc.vcycle(np.eye(N))
     assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+
+
+def test_red_black_sweep_is_gauss_seidel_in_colour_order():
+    """``order="rb"``: one forward sweep of the oracle (a triangular solve of the permuted matrix) is
+    the point Gauss-Seidel update written out node by node, colour 0 then colour 1, and, the colours
+    being independent sets of the 5-point matrix, also a Jacobi step on each colour in turn; the
+    backward sweep visits colour 1 first.  The cycle is symmetric and contracts the K_0 error."""
+    n = 9
+    s = p1.build(n, 1, 1, basis.LEGENDRE, 0.0)
+    H = p1.GSHierarchy(s.K[0], n, order="rb")
+    rng = np.random.default_rng(3)
+    for l, nl in enumerate(H.sizes[:-1]):
+        A = H.A[l].toarray()
+        m = nl - 2
+        x0, b = rng.standard_normal(m * m), rng.standard_normal(m * m)
+        colour = [((t % m) + (t // m)) % 2 for t in range(m * m)]
+        for forward, fac in ((True, H.low[l]), (False, H.up[l])):
+            got = H._sweep(fac, l, x0.copy(), b)
+            x = x0.copy()                               # node by node, in the sweep's order
+            order = [t for c in ((0, 1) if forward else (1, 0)) for t in range(m * m) if colour[t] == c]
+            if not forward:
+                order = [t for c in (1, 0) for t in reversed(range(m * m)) if colour[t] == c]
+            for t in order:
+                x[t] = (b[t] - sum(A[t, u] * x[u] for u in range(m * m) if u != t)) / A[t, t]
+            assert np.abs(got - x).max() <= 1e-13
+            y = x0.copy()                               # colour by colour, Jacobi on each colour
+            for c in ((0, 1) if forward else (1, 0)):
+                idx = [t for t in range(m * m) if colour[t] == c]
+                y[idx] += (b - A @ y)[idx] / np.diag(A)[idx]
+            assert np.abs(got - y).max() <= 1e-13
+    n = 17
+    s = p1.build(n, 1, 1, basis.LEGENDRE, 0.0)
+    H = p1.GSHierarchy(s.K[0], n, order="rb")
+    N = s.K[0].shape[0]
+    B = H.vcycle(np.eye(N))
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    E = np.eye(N) - B @ s.K[0].toarray()
+    assert max(abs(np.linalg.eigvals(E))) < 0.2
