@@ -100,13 +100,18 @@ typedef enum { SG_GMRES = 0, SG_FGMRES = 1, SG_GPCG = 2, SG_PCG = 3, SG_BGS = 4 
  * B = [A_hat 0; W D] with A_hat the Galerkin matrix of total degree p-1 solved by an inner
  * FGMRES (right-preconditioned by the flat B_T of A_hat, to inner_tol) and the degree-p
  * diagonal blocks D = I (x) K_0 by one V-cycle each (see sg_precond_blocktri_exact).
- * With FGMRES and pc_prec = SG_F64 only; an analysis form, each application costs a solve. */
+ * With FGMRES and pc_prec = SG_F64 only; an analysis form, each application costs a solve.
+ * SG_PC_BLOCKSYM_REC: the symmetric 2 x 2 form of Sec. 4.2, B_S = [A_hat 0; W D] diag(A_hat, D)^{-1}
+ * [A_hat W^T; 0 D], applied recursively over the degree levels (A_hat^{-1} replaced by the same
+ * preconditioner one degree lower, down to the mean block; D = I (x) K_0 by one V-cycle per block);
+ * symmetric, for PCG; pc_prec = SG_F64 only (see sg_precond_blocksym_rec). */
 typedef enum {
   SG_PC_NONE = 0,
   SG_PC_BLOCKTRI = 1,
   SG_PC_BLOCKDIAG = 2,
   SG_PC_BLOCKSYM = 3,
-  SG_PC_BLOCKTRI_EXACT = 4
+  SG_PC_BLOCKTRI_EXACT = 4,
+  SG_PC_BLOCKSYM_REC = 5
 } sg_pc;
 
 /* One SG problem (Sec. 2-3).  coef is a HOST array of (M+1) rows of (n-1)^2
@@ -134,8 +139,9 @@ typedef struct {
 } sg_problem;
 
 /* Solver options (Sec. 4.2, 6).  method: GMRES (right preconditioned) or
- * FGMRES (flexible: stores z_j = B^{-1} v_j in pc_prec) or GPCG[1] or PCG.
- * precond: block-triangular B_T, block-diagonal B_D or none.  restart: Krylov
+ * FGMRES (flexible: stores z_j = B^{-1} v_j in pc_prec) or GPCG[1] or PCG or the
+ * stationary block Gauss-Seidel iteration.  precond: sg_pc (B_T, B_D, B_S, the exact
+ * 2 x 2 B_T, the recursive 2 x 2 B_S, or none).  restart: Krylov
  * dimension m of (F)GMRES(m) (1..32).  maxit: maximum preconditioner
  * applications.  tol: stop when ||F - A U||_2 / ||F||_2 <= tol (true residual,
  * recomputed in FP64 at every restart and at the end).  pc_prec: precision of
@@ -256,6 +262,14 @@ int sg_precond_blocktri_exact(sg_handle h, const double* R, double* Z, int trans
 /* Z = B_S^{-1} R (Sec. 4.2): lower sweep, multiplication by the diagonal blocks K_0
  * (exact), upper sweep; symmetric positive definite, for PCG.  R FP64, Z in prec. */
 int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec);
+/* Z = B_S^{-1} R with the 2 x 2 symmetric form of Sec. 4.2 applied recursively over the degree levels:
+ * for the top degree q, y_low = B_{q-1}^{-1} R_low, y_q = D^{-1} (R_q - W y_low),
+ * z_low = B_{q-1}^{-1} (R_low - W^T y_q), Z = [z_low; y_q], with B_0^{-1} one V-cycle on the mean block
+ * and D^{-1} one V-cycle per block of degree q (W: the couplings of degree q to degree q - 1).  The
+ * degree-q' blocks are cycled 2^(p - q') times, so an application costs about twice a B_T sweep at
+ * p = 4.  R, Z: device FP64, P * N_x values (Z must not alias R).  Allocates a workspace of about p
+ * SG vectors on first use.  Stream-ordered; returns before the kernels finish. */
+int sg_precond_blocksym_rec(sg_handle h, const double* R, double* Z);
 /* One V(nu1,nu2) cycle on K_0 from a zero guess for nblocks stacked blocks of
  * N_x values: B FP64 (device), X in prec (device). */
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec);

@@ -163,6 +163,7 @@ int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec
   if (pc == SG_PC_BLOCKTRI) return precond_blocktri(h, rprec, R, Z, prec, transpose);
   if (pc == SG_PC_BLOCKDIAG) return precond_blockdiag(h, rprec, R, Z, prec);
   if (pc == SG_PC_BLOCKSYM) return precond_blocksym(h, rprec, R, Z, prec);
+  if (pc == SG_PC_BLOCKSYM_REC) return precond_blocksym_rec(h, rprec, R, Z, prec);
   return vec_cast(h, rprec, R, zprec_of(prec), Z, h->Nx * (size_t)h->P);
 }
 
@@ -246,8 +247,11 @@ struct OpsF64 {
   bool quant() const { return dfop && flexible && zprec_of(o.pc_prec) == SG_F32; }
   unsigned* qm(int j) const { return h->qmax + (size_t)j * h->P; }
   int precond(int j) {
+    h->zmax_out = quant() ? qm(j) : nullptr;
+    h->zmax_done = false;
     int rc = apply_precond(h, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose);
-    if (rc || !quant()) return rc;
+    h->zmax_out = nullptr;
+    if (rc || !quant() || h->zmax_done) return rc;
     return block_absmax(h, (const float*)z(j), qm(j));
   }
   int apply(int j) {
@@ -667,7 +671,7 @@ void destroy_ctx(sg_ctx* h) {
     h->child = nullptr;
   }
   cudaFree(h->xbuf);
-  cudaFree(h->ew), cudaFree(h->p1w);
+  cudaFree(h->ew), cudaFree(h->p1w), cudaFree(h->bsr);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
   cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->w64), cudaFree(h->pvec);
@@ -924,6 +928,12 @@ int sg_precond_blocksym(sg_handle h, const double* R, void* Z, int prec) {
   return precond_blocksym(h, SG_F64, R, Z, prec);
 }
 
+int sg_precond_blocksym_rec(sg_handle h, const double* R, double* Z) {
+  if (!h || !R || !Z) return h ? sg_fail(h, SG_E_ARG, "sg_precond_blocksym_rec: null argument") : SG_E_ARG;
+  if (const int rcd = sg_check_device(h, "sg_precond_blocksym_rec")) return rcd;
+  return precond_blocksym_rec(h, SG_F64, R, Z, SG_F64);
+}
+
 int sg_vcycle(sg_handle h, const double* B, void* X, int nblocks, int prec) {
   if (!h || !B || !X || prec < 0 || prec > 4 || prec == SG_DF64 || nblocks < 0 || nblocks > h->P)
     return h ? sg_fail(h, SG_E_ARG, "sg_vcycle: bad argument") : SG_E_ARG;
@@ -946,7 +956,7 @@ static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve
   if (!h || !F || !U || !opts) return h ? sg_fail(h, SG_E_ARG, "sg_solve: null argument") : SG_E_ARG;
   if (const int rcd = sg_check_device(h, "sg_solve")) return rcd;
   sg_solve_opts o = *opts;
-  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 4 || o.pc_prec < 0 || o.pc_prec > 4 ||
+  if (o.method < SG_GMRES || o.method > SG_BGS || o.precond < 0 || o.precond > 5 || o.pc_prec < 0 || o.pc_prec > 4 ||
       o.pc_prec == SG_DF64 ||
       !(o.tol > 0) || o.maxit < 0)
     return sg_fail(h, SG_E_ARG, "sg_solve: bad options");
@@ -959,6 +969,8 @@ static int solve_checked(sg_handle h, const double* F, double* U, const sg_solve
        o.inner_restart < 0 || o.inner_restart > 32))
     return sg_fail(h, SG_E_ARG, "sg_solve: the exact block-triangular preconditioner needs FGMRES in FP64 "
                                 "(pc_prec SG_F64, arith SG_ARITH_F64) and inner_restart <= 32");
+  if (o.precond == SG_PC_BLOCKSYM_REC && (o.pc_prec != SG_F64 || o.arith != SG_ARITH_F64))
+    return sg_fail(h, SG_E_ARG, "sg_solve: the recursive B_S is FP64 only (pc_prec SG_F64, arith SG_ARITH_F64)");
   if (h->elements == SG_P1 && (o.pc_prec != SG_F64 || o.arith != SG_ARITH_F64))
     return sg_fail(h, SG_E_ARG, "sg_solve: P1 elements solve in FP64 only (pc_prec SG_F64, arith SG_ARITH_F64)");
   h->inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-12;

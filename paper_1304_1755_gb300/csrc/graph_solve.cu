@@ -240,8 +240,12 @@ struct GSteps {
   int step(int j, cudaGraphConditionalHandle cn, bool has_next) {
     sg_ctx* H = h();
     int rc;
-    if ((rc = apply_precond_ext(H, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose))) return rc;
-    if (quant() && (rc = block_absmax(H, (const float*)z(j), qm(j)))) return rc;
+    H->zmax_out = quant() ? qm(j) : nullptr;
+    H->zmax_done = false;
+    rc = apply_precond_ext(H, o.precond, SG_F64, v(j), z(j), o.pc_prec, o.transpose);
+    H->zmax_out = nullptr;
+    if (rc) return rc;
+    if (quant() && !H->zmax_done && (rc = block_absmax(H, (const float*)z(j), qm(j)))) return rc;
     H->qcur = quant() ? qm(j) : nullptr;
     const int arith = o.arith == SG_ARITH_F64_DFOP ? SG_DF64 : SG_F64;
     if ((rc = launch_apply(H, 0, quant() ? SG_F32Q : zp(), z(j), 0, SG_F64, v(j + 1), 0, SG_F64, nullptr, 0, 0, H->P, 0,

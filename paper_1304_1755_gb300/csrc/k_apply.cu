@@ -58,6 +58,7 @@ struct ApplyArgs {
   int row0, nrows, ybase, rbase, n, m;
   size_t Nx, Nc;
   int nwx, nstrips, strip;   // warp columns (31 cells each), strips per output row, node rows per strip
+  int unit0;                 // every row's first term is the mean coupling with weight exactly 1
 };
 
 // ---- storage access --------------------------------------------------------
@@ -245,6 +246,12 @@ struct ArDF {
     dacc_fma(s.d2, w, f2);
     dacc_fma(s.hg, w, f3);
   }
+  // qterm with the weight exactly 1 on zero sums: the features themselves, no rounding error
+  static __device__ __forceinline__ void qterm_unit(State& s, float za, float zb, float zc, float zd, float q) {
+    s.d1 = {__fmul_rn(__fsub_rn(za, zc), q), 0.f};
+    s.d2 = {__fmul_rn(__fsub_rn(zb, zd), q), 0.f};
+    s.hg = {__fmul_rn(__fadd_rn(__fsub_rn(za, zb), __fsub_rn(zc, zd)), q), 0.f};
+  }
   static __device__ __forceinline__ df2 dsub(df2 a, df2 b) {
     float s, e;
     two_sum(a.hi, -b.hi, s, e);
@@ -408,8 +415,22 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
     const int e = cxw + cy * (n - 1);
     typename AR::State st;
     AR::init(st);
+    int t = 0;
+    if constexpr (std::is_same<AR, ArDF>::value && std::is_same<TXS, QF32>::value) {
+      if (a.unit0 && nt > 0) {
+        // the mean coupling: weight 1, so its exact grid features start the compensated sums as they
+        // are (the same values the general step would give, without its weight load and products)
+        const XE* p = rt.xp[0] + s_node;
+        const float sq = rt.qs[0];
+        const Z za = LX::ldq(p, xlo, oka), zb = LX::ldq(p + 1, xlo, okb);
+        const Z zc = LX::ldq(p + 1 + m, xlo, okc), zd = LX::ldq(p + m, xlo, okd);
+        AR::qterm_unit(st, __fmaf_rn(za.v, sq, SG_QBIAS), __fmaf_rn(zb.v, sq, SG_QBIAS),
+                       __fmaf_rn(zc.v, sq, SG_QBIAS), __fmaf_rn(zd.v, sq, SG_QBIAS), rt.qq[0]);
+        t = 1;
+      }
+    }
 #pragma unroll AR::kUnroll
-    for (int t = 0; t < nt; ++t) {
+    for (; t < nt; ++t) {
       const XE* p = rt.xp[t] + s_node;                     // vertex (cx, cy) of column j
       const T w = AR::template weight<WT>(ldg_ce(rt.wp[t] + e), rt.g[t]);
       const Z za = LX::ldq(p, xlo, oka);
@@ -655,6 +676,9 @@ int launch_apply(sg_ctx* h, int which, int xprec, const void* X, size_t xlo, int
   a.row_ptr = T.row_ptr, a.tj = T.j, a.tk = T.k, a.g64 = T.g, a.g32 = T.gf, a.gdf = (const df2*)T.gdf;
   a.row0 = row0, a.nrows = nrows, a.ybase = ybase, a.rbase = rbase, a.n = h->n, a.m = h->m;
   a.Nx = h->Nx, a.Nc = h->Nc;
+  // the mean coupling G_0(i, i) = 1 leads every row of the full and the diagonal tables; with the mean
+  // coefficient identically 1 its weight is exactly 1
+  a.unit0 = (which == 0 || which == 4) && h->const_mean;
   const int slot = arith == SG_F64 ? 0 : (arith == SG_DF64 ? 2 : 1);
   a.strip = h->apply_strip[slot] > 0 ? h->apply_strip[slot] : STRIP_DEFAULT;
   if (arith == SG_F64) return pick_x<ArF64>(h, a, xprec, yprec, rprec);

@@ -177,7 +177,8 @@ int run_down(sg_ctx* h, int l, int nb, const TB* b, TS* bc, bool bguard = false)
 }
 
 template <typename TB, typename TS, typename TA, typename TO = TS>
-int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TO* x, bool bguard = false, bool cguard = false) {
+int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TO* x, bool bguard = false, bool cguard = false,
+           unsigned* zmax = nullptr) {
   const MGLevel &F = h->lev[l], &C = h->lev[l + 1];
   if (h->const_mean && h->nu1 == 1 && h->nu2 == 1) {
     constexpr int FY = mu_fy<TB, TS, TA>();
@@ -185,11 +186,14 @@ int run_up(sg_ctx* h, int l, int nb, const TB* b, const TS* xc, TO* x, bool bgua
     const dim3 grid(tx * ty, nb);
     const TA c = (TA)(h->omega * 3.0 / 8.0);
     if (bguard && cguard)
-      mg_up_tile<TB, TS, TA, TO, true, true><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx);
+      mg_up_tile<TB, TS, TA, TO, true, true><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx,
+                                                                                zmax);
     else if (cguard)
-      mg_up_tile<TB, TS, TA, TO, false, true><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx);
+      mg_up_tile<TB, TS, TA, TO, false, true><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c,
+                                                                                 tx, zmax);
     else
-      mg_up_tile<TB, TS, TA, TO, false, false><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c, tx);
+      mg_up_tile<TB, TS, TA, TO, false, false><<<grid, MT_THREADS, 0, h->stream>>>(b, xc, x, F.m, C.m, F.N, C.N, F.N, c,
+                                                                                  tx, zmax);
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     return SG_OK;
@@ -237,8 +241,10 @@ int run_coarse(sg_ctx* h, int nb, const TB* b, TO* x) {
 
 // bguard: B lies in a guarded buffer; lguard: the level buffers of W are guarded (the handle's
 // workspace is, the static scratch of sg_vcycle_static is not).
+// zmax: see mg_up_tile (only on the tile path with levels below the fine grid; the caller checks)
 template <typename TB, typename TS, typename TA, typename TO = TS>
-int vcycle_t(sg_ctx* h, int nb, const TB* B, TO* X, PrecWork& W, bool bguard = false, bool lguard = false) {
+int vcycle_t(sg_ctx* h, int nb, const TB* B, TO* X, PrecWork& W, bool bguard = false, bool lguard = false,
+             unsigned* zmax = nullptr) {
   int rc;
   const int lc = h->lc;
   // descend
@@ -251,7 +257,7 @@ int vcycle_t(sg_ctx* h, int nb, const TB* B, TO* X, PrecWork& W, bool bguard = f
   else rc = run_coarse<TS, TS, TA>(h, nb, (const TS*)W.b[lc], (TS*)W.x[lc]);
   if (rc) return rc;
   for (int l = lc - 1; l >= 0; --l) {
-    if (l == 0) rc = run_up<TB, TS, TA, TO>(h, 0, nb, B, (const TS*)W.x[1], X, bguard, lguard);
+    if (l == 0) rc = run_up<TB, TS, TA, TO>(h, 0, nb, B, (const TS*)W.x[1], X, bguard, lguard, zmax);
     else rc = run_up<TS, TS, TA>(h, l, nb, (const TS*)W.b[l], (const TS*)W.x[l + 1], (TS*)W.x[l], lguard, lguard);
     if (rc) return rc;
   }
@@ -295,7 +301,7 @@ int ensure_prec_work(sg_ctx* h, int mode) {
   return SG_OK;
 }
 
-int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard) {
+int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard, unsigned* zmax) {
   if (nb <= 0) return SG_OK;
   if (nb > h->P) return sg_fail(h, SG_E_ARG, "vcycle: more blocks than the workspace holds");
   if (h->elements == SG_P1) {
@@ -306,17 +312,19 @@ int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, b
   if (rc) return rc;
   PrecWork& W = h->work[wprec_of(prec)];
   if (prec == SG_BF16Z) {                 // BF16 levels, FP32 output
-    if (bprec == SG_F64) return vcycle_t<double, bf16, float, float>(h, nb, (const double*)B, (float*)X, W, bguard, true);
-    if (bprec == SG_F32) return vcycle_t<float, bf16, float, float>(h, nb, (const float*)B, (float*)X, W, bguard, true);
-    return vcycle_t<bf16, bf16, float, float>(h, nb, (const bf16*)B, (float*)X, W, bguard, true);
+    if (bprec == SG_F64)
+      return vcycle_t<double, bf16, float, float>(h, nb, (const double*)B, (float*)X, W, bguard, true, zmax);
+    if (bprec == SG_F32)
+      return vcycle_t<float, bf16, float, float>(h, nb, (const float*)B, (float*)X, W, bguard, true, zmax);
+    return vcycle_t<bf16, bf16, float, float>(h, nb, (const bf16*)B, (float*)X, W, bguard, true, zmax);
   }
   if (prec == SG_F64) {
     if (bprec != SG_F64) return sg_fail(h, SG_E_ARG, "vcycle: FP64 cycle needs FP64 input");
     return vcycle_t<double, double, double>(h, nb, (const double*)B, (double*)X, W, bguard, true);
   }
   if (prec == SG_F32) {
-    if (bprec == SG_F64) return vcycle_t<double, float, float>(h, nb, (const double*)B, (float*)X, W, bguard, true);
-    return vcycle_t<float, float, float>(h, nb, (const float*)B, (float*)X, W, bguard, true);
+    if (bprec == SG_F64) return vcycle_t<double, float, float>(h, nb, (const double*)B, (float*)X, W, bguard, true, zmax);
+    return vcycle_t<float, float, float>(h, nb, (const float*)B, (float*)X, W, bguard, true, zmax);
   }
   if (bprec == SG_F64) return vcycle_t<double, bf16, float>(h, nb, (const double*)B, (bf16*)X, W, bguard, true);
   if (bprec == SG_F32) return vcycle_t<float, bf16, float>(h, nb, (const float*)B, (bf16*)X, W, bguard, true);
@@ -326,16 +334,17 @@ int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, b
 // A preconditioner application is a fixed sequence of about ten launches per degree
 // stage (many on tiny coarse grids), so on a non-default stream it is captured once
 // per operand set into a CUDA graph and replayed; the cache key is (R, Z, rprec,
-// prec, kind).  Nested capture by the caller falls back to direct launches.
+// prec, kind, the block-maxima output).  Nested capture by the caller falls back to direct launches.
 template <class Body>
-int run_graphed(sg_ctx* h, const void* R, const void* Z, int rprec, int prec, int kind, Body&& body) {
+int run_graphed(sg_ctx* h, const void* R, const void* Z, int rprec, int prec, int kind, Body&& body,
+                const void* zmax = nullptr) {
   int rc = ensure_prec_work(h, prec);
   if (rc) return rc;
   if (h->stream == nullptr) return body();
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SG_CUDA(h, cudaStreamIsCapturing(h->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return body();
-  const auto key = std::make_tuple(R, Z, rprec, prec, kind);
+  const auto key = std::make_tuple(R, Z, rprec, prec, kind, zmax);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     if (h->graphs.size() >= 512) {
@@ -366,8 +375,10 @@ int run_graphed(sg_ctx* h, const void* R, const void* Z, int rprec, int prec, in
 
 // B_T^{-1} (Sec. 4.2): degree levels q are dependent stages; the n_q diagonal
 // blocks of one stage are independent and cycled together.
-static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
+static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose,
+                                   unsigned* zmax) {
   int rc;
+  if (zmax) SG_CUDA(h, cudaMemsetAsync(zmax, 0, sizeof(unsigned) * h->P, h->stream));
   // storage of Z, of the work buffers and of the stage right-hand side T (FP32 for SG_BF16Z: the
   // levels stay BF16, the vectors the Krylov method sees are FP32)
   const int zp = zprec_of(prec), wp = wprec_of(prec), tp = prec == SG_BF16Z ? SG_F32 : wp;
@@ -378,13 +389,13 @@ static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z,
     const int r0 = h->lvl_off[q], nq = h->lvl_off[q + 1] - r0;
     char* Zq = (char*)Z + es * (size_t)r0 * h->Nx;
     if (s == 0) {
-      rc = vcycle_run(h, prec, nq, (const char*)R + rs * (size_t)r0 * h->Nx, rprec, Zq, false);
+      rc = vcycle_run(h, prec, nq, (const char*)R + rs * (size_t)r0 * h->Nx, rprec, Zq, false, zmax ? zmax + r0 : nullptr);
     } else {
       // T_q = R_q - sum over the couplings to the previous stage of G_k(i,j) K_k Z_j
       void* T = prec == SG_BF16Z ? h->work[wp].T32 : h->work[wp].T;
       rc = launch_apply(h, transpose ? 2 : 1, zp, Z, 0, tp, T, 0, rprec, R, 0, r0, nq, r0, 0, arith);
       if (rc) return rc;
-      rc = vcycle_run(h, prec, nq, T, tp, Zq, true);
+      rc = vcycle_run(h, prec, nq, T, tp, Zq, true, zmax ? zmax + r0 : nullptr);
     }
     if (rc) return rc;
   }
@@ -393,8 +404,17 @@ static int precond_blocktri_direct(sg_ctx* h, int rprec, const void* R, void* Z,
 
 int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose) {
   if (prec == SG_F64 && rprec != SG_F64) return sg_fail(h, SG_E_ARG, "blocktri: FP64 sweep needs FP64 input");
-  return run_graphed(h, R, Z, rprec, prec, transpose ? 2 : 1,
-                     [&] { return precond_blocktri_direct(h, rprec, R, Z, prec, transpose); });
+  // the output's block maxima come out of the level-0 up kernels when every stage takes that path
+  // (constant mean, V(1,1), a level below the fine grid, FP32 output)
+  unsigned* zmax = h->zmax_out && zprec_of(prec) == SG_F32 && h->elements == SG_Q1 && h->const_mean &&
+                           h->nu1 == 1 && h->nu2 == 1 && h->lc > 0
+                       ? h->zmax_out
+                       : nullptr;
+  const int rc = run_graphed(
+      h, R, Z, rprec, prec, transpose ? 2 : 1,
+      [&] { return precond_blocktri_direct(h, rprec, R, Z, prec, transpose, zmax); }, zmax);
+  h->zmax_done = rc == SG_OK && zmax;
+  return rc;
 }
 
 // B_S^{-1} (Sec. 4.2): B_S = B_T diag(A)^{-1} B_T^T, applied as a lower sweep, the exact
@@ -418,6 +438,39 @@ int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
   if ((rc = precond_blocktri(h, rprec, R, W.S1, prec, 0))) return rc;
   if ((rc = launch_apply(h, 4, zp, W.S1, 0, sprec, W.S2, 0, SG_F64, nullptr, 0, 0, h->P, 0, 0, sprec))) return rc;
   return precond_blocktri(h, sprec, W.S2, Z, prec, 1);
+}
+
+// B_S^{-1} in the recursive 2 x 2 form of Sec. 4.2 (FP64).  rec(q, R, Z): R holds the blocks of
+// degrees 0..q (block-contiguous from block 0), Z receives B_q^{-1} R in the same blocks.  Only degrees
+// q - 1 and q couple (G_k, k >= 1, changes one index by one), so W y_low reads the degree q - 1 blocks of
+// y_low and W^T y_q changes only the degree q - 1 rows of R_low; those rows go to a per-depth copy of
+// R_low.  Every step is an existing launch: the coupling tables' R - AX epilogue and the batched cycle.
+static int blocksym_rec(sg_ctx* h, int q, const double* R, double* Z) {
+  int rc;
+  const size_t Nx = h->Nx;
+  if (q == 0) return vcycle_run(h, SG_F64, 1, R, SG_F64, Z, false);
+  const int lo = h->lvl_off[q], nq = h->lvl_off[q + 1] - lo, l1 = h->lvl_off[q - 1], n1 = lo - l1;
+  if ((rc = blocksym_rec(h, q - 1, R, Z))) return rc;                       // y_low
+  double* T = (double*)h->work[SG_F64].T;                                     // R_q - W y_low
+  if ((rc = launch_apply(h, 1, SG_F64, Z, 0, SG_F64, T, 0, SG_F64, R, 0, lo, nq, lo, 0, SG_F64))) return rc;
+  if ((rc = vcycle_run(h, SG_F64, nq, T, SG_F64, Z + (size_t)lo * Nx, true))) return rc;   // y_q
+  double* Rl = h->bsr + h->bsr_off[q];                                        // R_low - W^T y_q
+  if (l1 > 0) SG_CUDA(h, cudaMemcpyAsync(Rl, R, sizeof(double) * Nx * l1, cudaMemcpyDeviceToDevice, h->stream));
+  if ((rc = launch_apply(h, 2, SG_F64, Z, 0, SG_F64, Rl + (size_t)l1 * Nx, 0, SG_F64, R, 0, l1, n1, l1, 0, SG_F64)))
+    return rc;
+  return blocksym_rec(h, q - 1, Rl, Z);                                       // z_low
+}
+
+int precond_blocksym_rec(sg_ctx* h, int rprec, const void* R, void* Z, int prec) {
+  if (rprec != SG_F64 || prec != SG_F64) return sg_fail(h, SG_E_ARG, "recursive B_S: FP64 only");
+  int rc = ensure_prec_work(h, SG_F64);
+  if (rc) return rc;
+  if (!h->bsr && h->p > 0) {               // per depth q >= 1: a copy of the blocks of degrees < q
+    size_t tot = 0;
+    for (int q = 1; q <= h->p; ++q) h->bsr_off[q] = tot, tot += (size_t)h->lvl_off[q] * h->Nx;
+    if (cudaMalloc(&h->bsr, sizeof(double) * tot) != cudaSuccess) return sg_fail(h, SG_E_ALLOC, "alloc recursive B_S work");
+  }
+  return run_graphed(h, R, Z, SG_F64, SG_F64, 3, [&] { return blocksym_rec(h, h->p, (const double*)R, (double*)Z); });
 }
 
 // B_D^{-1} (Sec. 4.1): one V-cycle on every PC block.

@@ -541,12 +541,17 @@ __global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, 
   double* Ub = U + (size_t)b * Nx;
   const float* Zb = Z + (size_t)b * Nx;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
+    // all NV loads first and unconditionally (slots past nz re-read the last column and carry a zero
+    // coefficient), so they are in flight together instead of one per accumulation step
+    float zv[NV];
+#pragma unroll
+    for (int l = 0; l < NV; ++l) zv[l] = Zb[(size_t)min(l, nz - 1) * ldz + s];
+    const double u0 = Ub[s];
     dacc a = dacc_zero();
 #pragma unroll
-    for (int l = 0; l < NV; ++l)
-      if (l < nz) dacc_fma(a, c[l], qgrid_value(Zb[(size_t)l * ldz + s], sc[l], qu[l]));
+    for (int l = 0; l < NV; ++l) dacc_fma(a, c[l], qgrid_value(zv[l], sc[l], qu[l]));
     const df2 r = dacc_get(a);
-    Ub[s] = (Ub[s] + (double)r.hi) + (double)r.lo;
+    Ub[s] = (u0 + (double)r.hi) + (double)r.lo;
   }
 }
 

@@ -17,6 +17,7 @@
 // plain loads, and never reads outside the array.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 namespace {
 constexpr int MT_THREADS = 256;
@@ -207,10 +208,12 @@ __global__ void __launch_bounds__(MT_THREADS) mg_down_tile(const TB* __restrict_
 // three-sums of g, and finishes the row below once the row above it is known -- one pass over the
 // windows with the partial sums in registers.
 // OB, OC: b, x_c lie in guarded arrays (load_window may over-fetch aligned chunks).
+// zmax (FP32 output only, may be null): per block, the largest |x| written, as float bits, merged by
+// atomicMax into zmax[block] (non-negative floats order like their bit patterns; a NaN wins).
 template <typename TB, typename TS, typename TA, typename TO = TS, bool OB = false, bool OC = false>
 __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ b, const TS* __restrict__ xc,
                                                          TO* __restrict__ x, int m, int mc, size_t ldb, size_t ldc,
-                                                         size_t ldx, TA c, int tiles_x) {
+                                                         size_t ldx, TA c, int tiles_x, unsigned* zmax = nullptr) {
   constexpr int MU_FY = mu_fy<TB, TS, TA>(), RW = MU_FY / 4;   // tile rows, rows per thread
   constexpr int NRB = MU_FY + 2, NCB = MU_FX + 2, SWB = win_pitch<TB, NCB>();
   constexpr int NRC = MU_FY / 2 + 3, NCC = MU_FX / 2 + 3, SWC = win_pitch<TS, NCC>();
@@ -243,6 +246,7 @@ __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ 
   TA Hm2[2] = {0, 0}, Hm1[2] = {0, 0}, gm1[2] = {0, 0}, bm1[2] = {0, 0};
   const int i0 = X0 + k0, i1 = i0 + 1;                         // fine columns of the outputs
   TO* xb = x + (size_t)blockIdx.y * ldx;
+  unsigned vmax = 0;                                           // |outputs| as float bits (FP32 output)
 #pragma unroll
   for (int k = 0; k < RW + 2; ++k) {
     const int r = jw + k;
@@ -266,14 +270,31 @@ __global__ void __launch_bounds__(MT_THREADS) mg_up_tile(const TB* __restrict__ 
       const int j = Y0 + r - 2;
       if (j < m) {
         TO* op = xb + (size_t)j * m;
-        if (i0 < m) st_as<TO, TA>(op + i0, alpha * gm1[0] + beta * bm1[0] + ((Hm2[0] + Hm1[0]) + H0));
-        if (i1 < m) st_as<TO, TA>(op + i1, alpha * gm1[1] + beta * bm1[1] + ((Hm2[1] + Hm1[1]) + H1));
+        const TA v0 = alpha * gm1[0] + beta * bm1[0] + ((Hm2[0] + Hm1[0]) + H0);
+        const TA v1 = alpha * gm1[1] + beta * bm1[1] + ((Hm2[1] + Hm1[1]) + H1);
+        if (i0 < m) st_as<TO, TA>(op + i0, v0);
+        if (i1 < m) st_as<TO, TA>(op + i1, v1);
+        if constexpr (std::is_same<TO, float>::value && std::is_same<TA, float>::value) {
+          if (i0 < m) vmax = max(vmax, __float_as_uint(fabsf(v0)));
+          if (i1 < m) vmax = max(vmax, __float_as_uint(fabsf(v1)));
+        }
       }
     }
     Hm2[0] = Hm1[0], Hm2[1] = Hm1[1];
     Hm1[0] = H0, Hm1[1] = H1;
     gm1[0] = g[1], gm1[1] = g[2];
     bm1[0] = bv[1], bm1[1] = bv[2];
+  }
+  if constexpr (std::is_same<TO, float>::value && std::is_same<TA, float>::value) {
+    if (zmax) {                                                // uniform over the grid
+      __shared__ unsigned cmax;
+      if (threadIdx.x == 0) cmax = 0;
+      for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      __syncthreads();
+      if (lane == 0 && vmax) atomicMax(&cmax, vmax);
+      __syncthreads();
+      if (threadIdx.x == 0 && cmax) atomicMax(zmax + blockIdx.y, cmax);
+    }
   }
 }
 }  // namespace

@@ -100,6 +100,13 @@ struct sg_ctx {
   bool const_mean = true;
   int elements = SG_Q1;                 // SG_Q1 or SG_P1 (the paper's triangles, point Gauss-Seidel cycle)
   int gs_order = SG_GS_LEX;             // SG_P1 smoother order (lexicographic or red-black)
+  // B_T applications with FP32 output may also record their output's per-block maxima (the grid scales
+  // of the flexible basis) in the level-0 multigrid kernels: the caller sets zmax_out, the sweep sets
+  // zmax_done when it did so
+  unsigned* zmax_out = nullptr;
+  bool zmax_done = false;
+  double* bsr = nullptr;                // recursive B_S: per depth q >= 1 a copy of the blocks of degree < q
+  size_t bsr_off[12] = {};              // (p <= 10)
   double* ew = nullptr;                 // SG_P1: edge weights per mode, (M+1) x 2 x n^2 (horizontal, vertical)
   double* p1w = nullptr;                // SG_P1: V-cycle workspace, P x p1w_ld doubles
   size_t p1w_ld = 0;
@@ -156,7 +163,7 @@ struct sg_ctx {
     cudaGraphExec_t exec;
     long long kernels;
   };
-  std::map<std::tuple<const void*, const void*, int, int, int>, GraphEntry> graphs;
+  std::map<std::tuple<const void*, const void*, int, int, int, const void*>, GraphEntry> graphs;
   std::string err;
 };
 
@@ -241,7 +248,8 @@ int setup_p1(sg_ctx* h);
 
 // k_mg.cu
 // bguard: B lies in a guarded buffer (sg_galloc), so the tile loaders may over-fetch around it
-int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard = false);
+int vcycle_run(sg_ctx* h, int prec, int nb, const void* B, int bprec, void* X, bool bguard = false,
+               unsigned* zmax = nullptr);
 // device buffers with 256 bytes before and 4 KB after the data, for the multigrid tile loaders
 void* sg_galloc(size_t bytes);
 void sg_gfree(void* p);
@@ -250,6 +258,7 @@ int ensure_prec_work(sg_ctx* h, int prec);
 int precond_blocktri(sg_ctx* h, int rprec, const void* R, void* Z, int prec, int transpose);
 int precond_blockdiag(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
 int precond_blocksym(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
+int precond_blocksym_rec(sg_ctx* h, int rprec, const void* R, void* Z, int prec);
 
 // k_vec.cu
 int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host);

@@ -18,7 +18,7 @@ LEGENDRE, HERMITE = 0, 1
 Q1, P1 = 0, 1                                   # sg_elements
 GS_LEX, GS_RB = 0, 1                            # sg_gs_order (P1 smoother)
 GMRES, FGMRES, GPCG, PCG, BGS = 0, 1, 2, 3, 4
-PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM, PC_BLOCKTRI_EXACT = 0, 1, 2, 3, 4
+PC_NONE, PC_BLOCKTRI, PC_BLOCKDIAG, PC_BLOCKSYM, PC_BLOCKTRI_EXACT, PC_BLOCKSYM_REC = 0, 1, 2, 3, 4, 5
 
 STATUS = {0: "SG_OK", -1: "SG_E_ARG", -2: "SG_E_ALLOC", -3: "SG_E_CUDA", -4: "SG_E_NOCONV",
           -5: "SG_E_BREAKDOWN", -6: "SG_E_NONFINITE", -7: "SG_E_TIMEOUT", -8: "SG_E_STATE"}
@@ -71,6 +71,7 @@ SIGNATURES = {
     "sg_precond_blocktri": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_precond_blockdiag": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
     "sg_precond_blocksym": (ctypes.c_int, [VP, VP, VP, ctypes.c_int]),
+    "sg_precond_blocksym_rec": (ctypes.c_int, [VP, VP, VP]),
     "sg_precond_blocktri_exact": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_double]),
     "sg_vcycle": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
     "sg_vcycle_static": (ctypes.c_int, [VP, VP, VP, ctypes.c_int, ctypes.c_int]),
@@ -214,6 +215,10 @@ class Handle:
 
     def precond_blocksym(self, R, Z, prec=F64):
         _check(lib().sg_precond_blocksym(self.h, _ptr(R), _ptr(Z), prec), self.h)
+
+    def precond_blocksym_rec(self, R, Z):
+        """sg_precond_blocksym_rec: the recursive 2 x 2 symmetric block preconditioner (FP64)."""
+        _check(lib().sg_precond_blocksym_rec(self.h, _ptr(R), _ptr(Z)), self.h)
 
     def vcycle(self, B, X, nblocks, prec=F64):
         _check(lib().sg_vcycle(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)

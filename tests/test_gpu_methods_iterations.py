@@ -42,10 +42,12 @@ def test_table3_methods_iterations_match_oracle(sigma):
         "BT-GPCG": krylov.gpcg1(Ax, bt, F, tol=1e-10, maxit=1000)[1],
         "BT-GMRes": krylov.gmres(Ax, bt, F, tol=1e-10, restart=10, maxit=1000)[1],
         "BS-PCG": krylov.pcg(Ax, lambda r: precond.block_sym_inv(s, solver, r), F, tol=1e-10, maxit=1000)[1],
+        "BS-PCG recursive": krylov.pcg(Ax, lambda r: precond.block_sym_recursive_inv(s, solver, r), F, tol=1e-10,
+                                       maxit=1000)[1],
     }
     methods = {"Block-GS": (sg.BGS, sg.PC_BLOCKTRI), "BD-PCG": (sg.PCG, sg.PC_BLOCKDIAG),
                "BT-GPCG": (sg.GPCG, sg.PC_BLOCKTRI), "BT-GMRes": (sg.GMRES, sg.PC_BLOCKTRI),
-               "BS-PCG": (sg.PCG, sg.PC_BLOCKSYM)}
+               "BS-PCG": (sg.PCG, sg.PC_BLOCKSYM), "BS-PCG recursive": (sg.PCG, sg.PC_BLOCKSYM_REC)}
     gpu = {}
     Fd = dev(F)
     for name, (meth, pc) in methods.items():
@@ -58,3 +60,20 @@ def test_table3_methods_iterations_match_oracle(sigma):
     for name in methods:
         assert abs(gpu[name] - oracle[name]) <= 1, (name, gpu[name], oracle[name])
     assert max(gpu["BT-GMRes"], gpu["BT-GPCG"], gpu["BS-PCG"]) < min(gpu["BD-PCG"], gpu["Block-GS"])
+
+
+def test_recursive_symmetric_preconditioner_matches_oracle():
+    """sg_precond_blocksym_rec against the oracle's recursion (every degree level's blocks cycled
+    2^(p - q) times), elementwise, and its symmetry <B^{-1} x, y> = <x, B^{-1} y>."""
+    import torch
+    from paper_1304_1755_gb300 import inputs
+    pr = Pair(65, 3, 3, basis.LEGENDRE, sigma=0.3)
+    X, Y = inputs.uniform(3, pr.N), inputs.uniform(4, pr.N)
+    ZX, ZY = dev(np.zeros(pr.N)), dev(np.zeros(pr.N))
+    pr.h.precond_blocksym_rec(dev(X), ZX)
+    pr.h.precond_blocksym_rec(dev(Y), ZY)
+    torch.cuda.synchronize()
+    want = precond.block_sym_recursive_inv(pr.sys, pr.oracle_vsolver(), X)
+    assert np.abs(host(ZX) - want).max() <= 1e-12 * np.abs(want).max()
+    a, b = float(np.dot(host(ZX), Y)), float(np.dot(X, host(ZY)))
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))

@@ -52,7 +52,7 @@ def test_operator_matches_oracle(n, M, p):
 @pytest.mark.parametrize("n,nu", [(17, (2, 2)), (65, (2, 2)), (129, (1, 1)), (257, (2, 1))])
 def test_vcycle_matches_oracle(order, n, nu):
     """One V-cycle from a zero guess on three blocks, every level and sweep order as the oracle's."""
-    pr = pair(n, 1, 1, 0.2, order, nu)
+    pr = pair(n, 2, 1, 0.2, order, nu)                   # P = 3 blocks
     Nx = pr.sys.Nx
     B = inputs.uniform(5, 3 * Nx).reshape(3, Nx)
     X = dev(np.zeros(3 * Nx))
@@ -73,6 +73,7 @@ def test_block_preconditioners_match_oracle(order):
          lambda: precond.block_tri_inv(pr.sys, pr.solver, R, transpose=True)),
         (lambda Z: pr.h.precond_blockdiag(Rd, Z), lambda: precond.block_diag_inv(pr.sys, pr.solver, R)),
         (lambda Z: pr.h.precond_blocksym(Rd, Z), lambda: precond.block_sym_inv(pr.sys, pr.solver, R)),
+        (lambda Z: pr.h.precond_blocksym_rec(Rd, Z), lambda: precond.block_sym_recursive_inv(pr.sys, pr.solver, R)),
     )
     for gpu, ora in cases:
         Z = dev(np.zeros(pr.N))
@@ -93,6 +94,9 @@ METHODS = {  # name: (sg method, sg precond, oracle run)
     "BS-PCG": (sg.PCG, sg.PC_BLOCKSYM,
                lambda A, pr, F: krylov.pcg(A, lambda r: precond.block_sym_inv(pr.sys, pr.solver, r), F,
                                            tol=1e-10, maxit=400)),
+    "BS-PCG recursive": (sg.PCG, sg.PC_BLOCKSYM_REC,
+                         lambda A, pr, F: krylov.pcg(A, lambda r: precond.block_sym_recursive_inv(pr.sys, pr.solver, r),
+                                                     F, tol=1e-10, maxit=400)),
     "Block-GS": (sg.BGS, sg.PC_BLOCKTRI,
                  lambda A, pr, F: krylov.block_gauss_seidel(A, lambda r: precond.block_tri_inv(pr.sys, pr.solver, r),
                                                             F, tol=1e-10, maxit=400)),
