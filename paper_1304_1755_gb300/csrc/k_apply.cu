@@ -146,6 +146,8 @@ struct ArF32 {
   static __device__ __forceinline__ void fma(Acc& s, T w, double z) { s = fmaf(w, (float)z, s); }
   static __device__ __forceinline__ void fma(Acc& s, T w, df2 z) { s = fmaf(w, z.hi, s); }
   static __device__ __forceinline__ T get(Acc s) { return s; }
+  static __device__ __forceinline__ T get_raw(Acc s) { return s; }
+  static __device__ __forceinline__ Acc acc_from(T x) { return x; }
   static __device__ __forceinline__ T add(T x, T y) { return x + y; }
   static __device__ __forceinline__ T sub(T x, T y) { return x - y; }
   static __device__ __forceinline__ T half(T x) { return 0.5f * x; }
@@ -174,6 +176,8 @@ struct ArF64 {
   static __device__ __forceinline__ void fma(Acc& s, T w, double z) { s = ::fma(w, z, s); }
   static __device__ __forceinline__ void fma(Acc& s, T w, df2 z) { s = ::fma(w, (double)z.hi + (double)z.lo, s); }
   static __device__ __forceinline__ T get(Acc s) { return s; }
+  static __device__ __forceinline__ T get_raw(Acc s) { return s; }
+  static __device__ __forceinline__ Acc acc_from(T x) { return x; }
   static __device__ __forceinline__ T add(T x, T y) { return x + y; }
   static __device__ __forceinline__ T sub(T x, T y) { return x - y; }
   static __device__ __forceinline__ T half(T x) { return 0.5 * x; }
@@ -202,6 +206,10 @@ struct ArDF {
   static __device__ __forceinline__ void fma(Acc& s, T w, df2 z) { dacc_fma(s, w, z); }
   static __device__ __forceinline__ void fma(Acc& s, T w, double z) { dacc_fma(s, w, df_from_double(z)); }
   static __device__ __forceinline__ T get(Acc s) { return dacc_get(s); }
+  // the pair (s, c) without the final TwoSum: hi + lo is still the value (|c| is a few ulp of s), which
+  // is all a further compensated sum or an FP64 store needs
+  static __device__ __forceinline__ T get_raw(Acc s) { return {s.s, s.c}; }
+  static __device__ __forceinline__ Acc acc_from(T x) { return dacc_from(x); }
   static __device__ __forceinline__ T add(T x, T y) { return df_add(x, y); }
   static __device__ __forceinline__ T sub(T x, T y) { return df_sub(x, y); }
   static __device__ __forceinline__ T half(T x) { return df_scale2(x, 0.5f); }
@@ -273,9 +281,9 @@ struct ArDF {
     term(s, w, df_from_double(za), df_from_double(zb), df_from_double(zc), df_from_double(zd));
   }
   static __device__ __forceinline__ void features(State& s, T& A, T& B, T& C) {
-    A = half(dacc_get(s.d1));
-    B = half(dacc_get(s.d2));
-    C = sixth(dacc_get(s.hg));
+    A = half(get_raw(s.d1));       // consumed only by compensated sums: no renormalisation needed
+    B = half(get_raw(s.d2));
+    C = sixth(get_raw(s.hg));
   }
 };
 
@@ -450,21 +458,21 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs a) {
     if (cy > cy0) {
       // this lane's cells seen from node (cx + 1, cy): SE corner of cell (cx, cy) and NE corner of
       // cell (cx, cy - 1); sent to the right neighbour
-      Acc u = AR::zero();
-      AR::acc_add(u, Bc);
+      Acc u = AR::acc_from(Bc);
       AR::acc_sub(u, Cc);
       AR::acc_add(u, Cp);
       AR::acc_sub(u, Ap);
-      const T ul = shfl_up1(AR::get(u));
+      const T ul = shfl_up1(AR::get_raw(u));
       if (out) {
         // node (cx, cy): SW corner of cell (cx, cy), NW corner of cell (cx, cy - 1), plus the left lane
-        Acc y = AR::zero();
-        AR::acc_add(y, Ac);
+        Acc y = AR::acc_from(Ac);
         AR::acc_add(y, Cc);
         AR::acc_sub(y, Bp);
         AR::acc_sub(y, Cp);
         AR::acc_add(y, ul);
-        Store<TYS>::put(a.Y, a.ylo, (size_t)(i - a.ybase) * a.Nx + s_node, E::f(rv, AR::get(y)));
+        // an FP64 store rounds hi + lo once either way; other outputs take the renormalised pair
+        const T yv = std::is_same<TYS, double>::value ? AR::get_raw(y) : AR::get(y);
+        Store<TYS>::put(a.Y, a.ylo, (size_t)(i - a.ybase) * a.Nx + s_node, E::f(rv, yv));
       }
     }
     Ap = Ac, Bp = Bc, Cp = Cc;
