@@ -155,11 +155,7 @@ typedef struct {
  * 1 classical Gram-Schmidt with a second pass when the norm drops by more than
  * 1/sqrt(2) (selective reorthogonalisation).  arith: sg_arith.  inner_tol, inner_restart:
  * tolerance (0 selects 1e-12) and restart (0 selects 30) of the inner solves of
- * SG_PC_BLOCKTRI_EXACT; ignored by the other preconditioners.  serial_gs: 0 (default) lets FGMRES
- * with an FP64 basis overlap the FP64-bound Gram-Schmidt dot products with the outer operator (the
- * operator in row chunks, each chunk's dot products on a high-priority side stream of the handle as soon
- * as it is written; the sums are the same numbers added in another order); 1 runs them one after the
- * other on the handle's stream. */
+ * SG_PC_BLOCKTRI_EXACT; ignored by the other preconditioners. */
 typedef struct {
   int method;
   int precond;
@@ -173,7 +169,6 @@ typedef struct {
   int arith;
   double inner_tol;
   int inner_restart;
-  int serial_gs;
 } sg_solve_opts;
 
 /* Filled by sg_solve. iters = preconditioner applications (Arnoldi steps);

@@ -264,32 +264,6 @@ struct OpsF64 {
   }
   int dots(int j, bool ww) { return vec_dots(h, V, h->Np, j + 1, v(j + 1), h->Np, ww, nullptr); }
   int axpys(int j, const double* c) { return vec_axpys_norm(h, V, h->Np, j + 1, c, v(j + 1), h->Np, nullptr); }
-  // The outer operator is FP32-bound (double-float) or FP64-bound, the Gram-Schmidt dot products are
-  // FP64-bound: w = A z_j is formed in SG_GS_CHUNKS row chunks on the handle's stream and each chunk's
-  // dot products V^T w, w.w run on the high-priority side stream as soon as the chunk is written, so the
-  // two kinds of work share the SMs.  Chunk boundaries are even rows, so every chunk's vectors start on
-  // a 16-byte boundary (N_x is odd); the last chunk runs to the padded length.  dv: V^T w, then w.w.
-  bool overlap_dots() const { return flexible && h->P >= 2 * SG_GS_CHUNKS && !o.serial_gs; }
-  int apply_dots(int j, double* dv) {
-    int rc = ensure_gs_stream(h);
-    if (rc) return rc;
-    h->qcur = quant() ? qm(j) : nullptr;
-    const int xprec = quant() ? SG_F32Q : zprec_of(o.pc_prec), arith = dfop ? SG_DF64 : SG_F64;
-    const size_t Nx = h->Nx;
-    int slots = 0;
-    for (int c = 0; c < SG_GS_CHUNKS; ++c) {
-      const int r0 = (c * h->P / SG_GS_CHUNKS) / 2 * 2;
-      const int r1 = c + 1 == SG_GS_CHUNKS ? h->P : ((c + 1) * h->P / SG_GS_CHUNKS) / 2 * 2;
-      if (r1 <= r0) continue;
-      if ((rc = launch_apply(h, 0, xprec, z(j), 0, SG_F64, v(j + 1), 0, SG_F64, nullptr, 0, r0, r1 - r0, 0, 0, arith)))
-        return rc;
-      SG_CUDA(h, cudaEventRecord(h->gs_ev[slots], h->stream));
-      const size_t e0 = (size_t)r0 * Nx, e1 = c + 1 == SG_GS_CHUNKS ? h->Np : (size_t)r1 * Nx;
-      if ((rc = vec_dots_chunk(h, slots, V + e0, h->Np, j + 1, v(j + 1) + e0, e1 - e0, true))) return rc;
-      ++slots;
-    }
-    return gs_collect(h, slots, j + 2, dv);
-  }
   int update(int k, const double* y) {
     int rc0 = spec_invalidate(h);
     if (rc0) return rc0;
@@ -369,8 +343,6 @@ struct OpsDF {
                         nullptr, 0, 0, h->P, 0, 0, SG_DF64);
   }
   int dots(int j, bool ww) { return df_dots(h, V, 2 * h->Np, j + 1, v(j + 1), h->Np, ww); }
-  bool overlap_dots() const { return false; }
-  int apply_dots(int, double*) { return SG_E_ARG; }
   int axpys(int j, const double* c) { return df_axpys_norm(h, V, 2 * h->Np, j + 1, c, v(j + 1), h->Np); }
   int update(int k, const double* y) {
     if (quant()) return df_update_q(h, Ud, h->Np, (const float*)h->kz, h->Np, k, y, N, h->qmax);
@@ -428,21 +400,16 @@ int solve_gmres_t(sg_ctx* h, Ops& ops, const sg_solve_opts& o, sg_solve_info& in
         PhaseScope ps(h, 1);
         if ((rc = ops.precond(j))) return rc;                  // z_j / s_j = B^{-1} (stored v_j)
       }
-      // classical Gram-Schmidt on the stored vectors: d = V^T w (and w.w), w -= V (s^2 d), ||w||^2
-      if (ops.overlap_dots()) {
-        PhaseScope ps(h, 0);                                   // operator and overlapped dot products
-        if ((rc = ops.apply_dots(j, dv.data()))) return rc;
-      } else {
-        {
-          PhaseScope ps(h, 0);
-          if ((rc = ops.apply(j))) return rc;                  // w / s_j = A z_j / s_j, stored in v_{j+1}
-        }
-        {
-          PhaseScope ps(h, 2);
-          if ((rc = ops.dots(j, true))) return rc;
-        }
-        if ((rc = copy_red(h, 0, j + 2, dv.data()))) return rc;
+      {
+        PhaseScope ps(h, 0);
+        if ((rc = ops.apply(j))) return rc;                    // w / s_j = A z_j / s_j, stored in v_{j+1}
       }
+      // classical Gram-Schmidt on the stored vectors: d = V^T w (and w.w), w -= V (s^2 d), ||w||^2
+      {
+        PhaseScope ps(h, 2);
+        if ((rc = ops.dots(j, true))) return rc;
+      }
+      if ((rc = copy_red(h, 0, j + 2, dv.data()))) return rc;
       for (int i = 0; i <= j; ++i) coef[i] = sc[i] * sc[i] * dv[i];
       if ((rc = upload_red(h, 3, coef.data(), j + 1))) return rc;
       double nrm2 = 0;
@@ -705,10 +672,6 @@ void destroy_ctx(sg_ctx* h) {
   }
   cudaFree(h->xbuf);
   cudaFree(h->ew), cudaFree(h->p1w), cudaFree(h->bsr);
-  if (h->gs_stream) cudaStreamDestroy(h->gs_stream);
-  for (auto& e : h->gs_ev)
-    if (e) cudaEventDestroy(e);
-  cudaFree(h->gs_partial), cudaFree(h->gs_out), cudaFree(h->gs_count), cudaFreeHost(h->gs_host);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
   cudaFree(h->coef64), cudaFree(h->coef32), cudaFree(h->coefdf), cudaFree(h->wdf), cudaFree(h->w64), cudaFree(h->pvec);

@@ -377,62 +377,6 @@ static int red_grid(sg_ctx* h, size_t N) {
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)h->red_blocks, (N + NT - 1) / NT));
 }
 
-// The side stream of the overlapped Gram-Schmidt dot products (created once per handle, with the
-// device's highest stream priority so that its FP64-bound blocks are scheduled as soon as the
-// FP32-bound operator's blocks leave room) and its own reduction set.
-int ensure_gs_stream(sg_ctx* h) {
-  if (h->gs_stream) return SG_OK;
-  int lo = 0, hi = 0;
-  SG_CUDA(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
-  SG_CUDA(h, cudaStreamCreateWithPriority(&h->gs_stream, cudaStreamNonBlocking, hi));
-  for (auto& e : h->gs_ev) SG_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  const int rb = 152 * 8;
-  if (cudaMalloc(&h->gs_partial, sizeof(double) * MAXOUT * rb) != cudaSuccess ||
-      cudaMalloc(&h->gs_out, sizeof(double) * SG_GS_CHUNKS * MAXOUT) != cudaSuccess ||
-      cudaMalloc(&h->gs_count, sizeof(unsigned) * 8) != cudaSuccess ||
-      cudaMallocHost(&h->gs_host, sizeof(double) * SG_GS_CHUNKS * MAXOUT) != cudaSuccess)
-    return sg_fail(h, SG_E_ALLOC, "alloc Gram-Schmidt side buffers");
-  SG_CUDA(h, cudaMemsetAsync(h->gs_count, 0, sizeof(unsigned) * 8, h->gs_stream));
-  SG_CUDA(h, cudaStreamSynchronize(h->gs_stream));
-  return SG_OK;
-}
-
-// Chunk `chunk` of V^T w (and w.w): elements [0, N) of the given (offset) vectors, on the side stream
-// after the handle's stream reached gs_ev[chunk] (the caller records it once the chunk's rows of w are
-// written); the sums land in output slot `chunk`.
-int vec_dots_chunk(sg_ctx* h, int chunk, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww) {
-  if (nv < 0 || nv > 32 || chunk < 0 || chunk >= SG_GS_CHUNKS) return sg_fail(h, SG_E_ARG, "dots chunk: bad arguments");
-  SG_CUDA(h, cudaStreamWaitEvent(h->gs_stream, h->gs_ev[chunk], 0));
-  const int g = (int)std::max<size_t>(1, std::min<size_t>((size_t)152 * 8, (N + NT - 1) / NT));
-  double* out = h->gs_out + (size_t)chunk * MAXOUT;
-  switch (nv) {
-    case 0: k_dots<0><<<g, NT, 0, h->gs_stream>>>(V, ldv, w, N, with_ww, h->gs_partial, out, h->gs_count); break;
-#define SG_C(K) \
-    case K: k_dots<K><<<g, NT, 0, h->gs_stream>>>(V, ldv, w, N, with_ww, h->gs_partial, out, h->gs_count); break;
-    SG_NV_CASES(SG_C)
-#undef SG_C
-  }
-  SG_CUDA(h, cudaGetLastError());
-  count_launch(h);
-  return SG_OK;
-}
-
-// Sums the first nout outputs of chunks 0..nchunks-1 in chunk order (deterministic) on the host, and
-// makes the handle's stream wait for the side stream.
-int gs_collect(sg_ctx* h, int nchunks, int nout, double* out_host) {
-  SG_CUDA(h, cudaMemcpyAsync(h->gs_host, h->gs_out, sizeof(double) * MAXOUT * nchunks, cudaMemcpyDeviceToHost,
-                             h->gs_stream));
-  SG_CUDA(h, cudaEventRecord(h->gs_ev[SG_GS_CHUNKS], h->gs_stream));
-  SG_CUDA(h, cudaStreamWaitEvent(h->stream, h->gs_ev[SG_GS_CHUNKS], 0));
-  SG_CUDA(h, cudaStreamSynchronize(h->gs_stream));
-  for (int o = 0; o < nout; ++o) {
-    double s = 0;
-    for (int c = 0; c < nchunks; ++c) s += h->gs_host[(size_t)c * MAXOUT + o];
-    out_host[o] = s;
-  }
-  return SG_OK;
-}
-
 // h[0..nv) = V^T w (and w.w in slot nv when with_ww), result left in red_out[0..] on the device and,
 // when out_host != nullptr, copied to the host (synchronising the stream).
 int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host) {

@@ -37,7 +37,6 @@ __device__ __forceinline__ float qgrid_quantum(unsigned maxbits) {
 #endif
 #define SG_QBIAS 12582912.0f   // 1.5 * 2^23
 #define SG_MAX_RESTART 64
-#define SG_GS_CHUNKS 4
 #define SG_NTHREADS_RED 256
 
 // Scalar load/store with conversion to the arithmetic type.
@@ -156,14 +155,6 @@ struct sg_ctx {
   // residual is being checked, since the check usually confirms convergence.
   double* spec_dst = nullptr;           // host destination of U (null: no early copy)
   cudaStream_t cstream = nullptr;       // side stream of the early copy
-  // FP64 Gram-Schmidt dot products overlapped with the FP32-bound outer operator: the operator runs in
-  // row chunks on the handle's stream, each chunk's dot products on this high-priority side stream
-  cudaStream_t gs_stream = nullptr;
-  cudaEvent_t gs_ev[SG_GS_CHUNKS + 1] = {};
-  double* gs_partial = nullptr;         // reduction set of the side stream (partials, per-chunk outputs)
-  double* gs_out = nullptr;
-  unsigned* gs_count = nullptr;
-  double* gs_host = nullptr;
   cudaEvent_t ev_u = nullptr, ev_c = nullptr;   // U ready / copy done
   bool spec_pending = false;            // an early copy was issued and U has not changed since
   int apply_strip[3] = {0, 0, 0};       // operator kernel strip height per arithmetic (FP64, FP32, DF); 0 = default
@@ -271,9 +262,6 @@ int precond_blocksym_rec(sg_ctx* h, int rprec, const void* R, void* Z, int prec)
 
 // k_vec.cu
 int vec_dots(sg_ctx* h, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww, double* out_host);
-int ensure_gs_stream(sg_ctx* h);
-int vec_dots_chunk(sg_ctx* h, int chunk, const double* V, size_t ldv, int nv, const double* w, size_t N, bool with_ww);
-int gs_collect(sg_ctx* h, int nchunks, int nout, double* out_host);
 int vec_axpys_norm(sg_ctx* h, const double* V, size_t ldv, int nv, const double* hcoef_dev, double* w, size_t N,
                    double* nrm2_host);
 int vec_update(sg_ctx* h, double* U, int zprec, const void* Z, size_t ldz, int nz, const double* y_host, size_t N);

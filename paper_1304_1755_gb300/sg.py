@@ -40,8 +40,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("precond", ctypes.c_int), ("restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("pc_prec", ctypes.c_int),
                 ("transpose", ctypes.c_int), ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int),
-                ("arith", ctypes.c_int), ("inner_tol", ctypes.c_double), ("inner_restart", ctypes.c_int),
-                ("serial_gs", ctypes.c_int)]
+                ("arith", ctypes.c_int), ("inner_tol", ctypes.c_double), ("inner_restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -230,10 +229,9 @@ class Handle:
         _check(lib().sg_vcycle_static(self.h, _ptr(B), _ptr(X), nblocks, prec), self.h)
 
     def solve(self, F, U, method=FGMRES, precond=PC_BLOCKTRI, restart=30, maxit=500, tol=1e-8, pc_prec=F64,
-              transpose=False, x0_given=False, reorth=0, arith=ARITH_F64, check=True, inner_tol=0.0, inner_restart=0,
-              serial_gs=False):
+              transpose=False, x0_given=False, reorth=0, arith=ARITH_F64, check=True, inner_tol=0.0, inner_restart=0):
         o = SolveOpts(method, precond, restart, maxit, tol, pc_prec, int(transpose), int(x0_given), reorth, arith,
-                      inner_tol, inner_restart, int(serial_gs))
+                      inner_tol, inner_restart)
         info = SolveInfo()
         rc = lib().sg_solve(self.h, _ptr(F), _ptr(U), ctypes.byref(o), ctypes.byref(info))
         if check and rc not in (0,):

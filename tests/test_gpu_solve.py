@@ -332,25 +332,3 @@ def test_exact_lower_block_preconditioner_matches_oracle():
     its_flat = pr.h.solve(dev(F), torch.zeros_like(U), method=sg.FGMRES, precond=sg.PC_BLOCKTRI, pc_prec=sg.F64,
                           tol=1e-12, restart=30).iters
     assert info.iters <= its_flat                          # the exact lower block is the stronger preconditioner
-
-
-@pytest.mark.parametrize("arith,pcp", [(sg.ARITH_F64_DFOP, sg.BF16Z), (sg.ARITH_F64, sg.F32), (sg.ARITH_F64, sg.F64)])
-def test_overlapped_gram_schmidt_matches_serial(arith, pcp):
-    """FGMRES with the Gram-Schmidt dot products overlapped with the outer operator (chunked, on the
-    handle's side stream) against the same solve run one step after the other: the dot products are the
-    same numbers summed in another order, so the iterations agree to within one and the solutions to
-    rounding; both reach the direct solution."""
-    import torch
-    pr = Pair(129, 3, 3, basis.HERMITE, sigma=0.3)            # P = 20 blocks: four chunks of even rows
-    F = osg.rhs(pr.sys, inputs.rhs_nodes(5, 129))
-    Ustar = _direct(pr, F)
-    out = []
-    for serial in (False, True):
-        U = torch.zeros(pr.N, dtype=torch.float64, device="cuda")
-        info = pr.h.solve(dev(F), U, pc_prec=pcp, tol=1e-10, restart=20, arith=arith, serial_gs=serial)
-        torch.cuda.synchronize()
-        assert info.status == 0 and info.relres_true <= 1e-10
-        assert np.linalg.norm(host(U) - Ustar) <= (1e-8 if pcp == sg.F64 else 1e-6) * np.linalg.norm(Ustar)
-        out.append((info.iters, host(U)))
-    assert abs(out[0][0] - out[1][0]) <= 1
-    assert np.linalg.norm(out[0][1] - out[1][1]) <= 1e-8 * np.linalg.norm(out[1][1])
