@@ -422,7 +422,12 @@ def run_ours(args, wl, rank, world):
         "unit": "GB/s",
         "frac": round(k1_gbs / hbm, 4),
         "peak_source": hbm_src,
-        "traffic": None,
+        # DRAM bytes of one launch of this kernel in an ncu capture of the 513^2 copy (P = 210, 54,835,410
+        # unknowns: 274.03 MB read + 396.30 MB written), scaled to this workload by unknowns; only for
+        # the configured form, whose kernel the capture measured
+        "traffic": (round(670.34e6 * N / 54835410) if arith == sg.ARITH_F64_DFOP and wl["pc_prec"] == sg.BF16Z
+                    else None),
+        "traffic_source": "ncu capture of the 513^2 copy, scaled by unknowns",
         "algorithmic_bytes_per_launch": bytes_k1,
         "launch_ms": round(k1_launch_ms, 4),
         "launches": n_k1,
