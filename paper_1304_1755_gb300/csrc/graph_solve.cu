@@ -158,26 +158,30 @@ __global__ void k_g_update_q(double* __restrict__ U, const float* __restrict__ Z
   const int b = blockIdx.y;
   const int nz = min(d->k - c0, NV);
   if (nz <= 0) return;
-  df2 c[NV];
-  float sc[NV], qu[NV];
-#pragma unroll
-  for (int l = 0; l < NV; ++l) {
-    c[l] = df_from_double((l < nz) ? d->y[c0 + l] : 0.0);
-    const unsigned mb = (l < nz) ? qmax[(size_t)(c0 + l) * P + b] : 0u;
-    sc[l] = qgrid_scale(mb), qu[l] = qgrid_quantum(mb);
+  // per column: y_l as double-float, the block's grid scale and quantum (zero past nz), once per CTA in
+  // shared memory; every column load is issued before the sums (slots past nz re-read the last column)
+  __shared__ float4 kc[NV];
+  for (int l = threadIdx.x; l < NV; l += blockDim.x) {
+    const df2 c = df_from_double(l < nz ? d->y[c0 + l] : 0.0);
+    const unsigned mb = l < nz ? qmax[(size_t)(c0 + l) * P + b] : 0u;
+    kc[l] = make_float4(c.hi, c.lo, qgrid_scale(mb), qgrid_quantum(mb));
   }
+  __syncthreads();
   double* Ub = U + (size_t)b * Nx;
   const float* Zb = Z + (size_t)c0 * ldz + (size_t)b * Nx;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
+    float zv[NV];
+#pragma unroll
+    for (int l = 0; l < NV; ++l) zv[l] = Zb[(size_t)min(l, nz - 1) * ldz + s];
+    const double u0 = Ub[s];
     dacc a = dacc_zero();
 #pragma unroll
-    for (int l = 0; l < NV; ++l)
-      if (l < nz) {
-        const float z = Zb[(size_t)l * ldz + s];
-        dacc_fma(a, c[l], __fmul_rn(__fsub_rn(__fmaf_rn(z, sc[l], SG_QBIAS), SG_QBIAS), qu[l]));
-      }
+    for (int l = 0; l < NV; ++l) {
+      const float4 k = kc[l];
+      dacc_fma(a, df2{k.x, k.y}, __fmul_rn(__fsub_rn(__fmaf_rn(zv[l], k.z, SG_QBIAS), SG_QBIAS), k.w));
+    }
     const df2 r = dacc_get(a);
-    Ub[s] = (Ub[s] + (double)r.hi) + (double)r.lo;
+    Ub[s] = (u0 + (double)r.hi) + (double)r.lo;
   }
 }
 
@@ -200,16 +204,25 @@ __global__ void k_g_update(double* __restrict__ U, const TZ* __restrict__ Z, siz
       U[i] = u;
     }
   } else {                       // as k_update: the sum in double-float, one FP64 addition
-    df2 c[NV];
-#pragma unroll
-    for (int l = 0; l < NV; ++l) c[l] = df_from_double((l < nz) ? d->y[c0 + l] : 0.0);
+    __shared__ float2 kc[NV];
+    for (int l = threadIdx.x; l < NV; l += blockDim.x) {
+      const df2 c = df_from_double(l < nz ? d->y[c0 + l] : 0.0);
+      kc[l] = make_float2(c.hi, c.lo);
+    }
+    __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+      float zv[NV];
+#pragma unroll
+      for (int l = 0; l < NV; ++l) zv[l] = ld_as<float>(Zc + (size_t)min(l, nz - 1) * ldz + i);
+      const double u0 = U[i];
       dacc a = dacc_zero();
 #pragma unroll
-      for (int l = 0; l < NV; ++l)
-        if (l < nz) dacc_fma(a, c[l], ld_as<float>(Zc + (size_t)l * ldz + i));
+      for (int l = 0; l < NV; ++l) {
+        const float2 k = kc[l];
+        dacc_fma(a, df2{k.x, k.y}, zv[l]);
+      }
       const df2 r = dacc_get(a);
-      U[i] = (U[i] + (double)r.hi) + (double)r.lo;
+      U[i] = (u0 + (double)r.hi) + (double)r.lo;
     }
   }
 }

@@ -250,17 +250,28 @@ __global__ void k_update(double* __restrict__ U, const TZ* __restrict__ Z, size_
       U[i] = u;
     }
   } else {
-    // FP32 / BF16 z: the sum over l in double-float (FP32 instructions), added to U in FP64 once
-    df2 c[NV];
-#pragma unroll
-    for (int l = 0; l < NV; ++l) c[l] = df_from_double((l < nz) ? y[l] : 0.0);
+    // FP32 / BF16 z: the sum over l in double-float (FP32 instructions), added to U in FP64 once.  The
+    // coefficients as double-float sit in shared memory (zero past nz), formed once per CTA; every
+    // column load is issued before the sums (slots past nz re-read the last column).
+    __shared__ float2 kc[NV];
+    for (int l = threadIdx.x; l < NV; l += blockDim.x) {
+      const df2 c = df_from_double(l < nz ? y[l] : 0.0);
+      kc[l] = make_float2(c.hi, c.lo);
+    }
+    __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+      float zv[NV];
+#pragma unroll
+      for (int l = 0; l < NV; ++l) zv[l] = ld_as<float>(Z + (size_t)min(l, nz - 1) * ldz + i);
+      const double u0 = U[i];
       dacc a = dacc_zero();
 #pragma unroll
-      for (int l = 0; l < NV; ++l)
-        if (l < nz) dacc_fma(a, c[l], ld_as<float>(Z + (size_t)l * ldz + i));
+      for (int l = 0; l < NV; ++l) {
+        const float2 k = kc[l];
+        dacc_fma(a, df2{k.x, k.y}, zv[l]);
+      }
       const df2 r = dacc_get(a);
-      U[i] = (U[i] + (double)r.hi) + (double)r.lo;
+      U[i] = (u0 + (double)r.hi) + (double)r.lo;
     }
   }
 }
@@ -527,29 +538,32 @@ __device__ __forceinline__ float qgrid_value(float z, float s, float q) {
 // accumulated in double-float from the exact FP32 grid values (FP32 instructions; an FP64 multiply-add per
 // term would make this pass FP64-bound on GB300) and added to U in FP64 once.
 template <int NV>
-__global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, size_t ldz, int nz,
+__global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, size_t ldz,
                            const double* __restrict__ y, size_t Nx, const unsigned* __restrict__ qmax, int P) {
   const int b = blockIdx.y;
-  df2 c[NV];
-  float sc[NV], qu[NV];
-#pragma unroll
-  for (int l = 0; l < NV; ++l) {
-    c[l] = df_from_double((l < nz) ? y[l] : 0.0);
-    const unsigned mb = (l < nz) ? qmax[(size_t)l * P + b] : 0u;
-    sc[l] = qgrid_scale(mb), qu[l] = qgrid_quantum(mb);
+  // per column: the coefficient y_l as double-float and the block's grid scale and quantum, formed once
+  // per CTA in shared memory (held in registers they would be re-derived, with FP64 work, per element)
+  __shared__ float4 kc[NV];
+  for (int l = threadIdx.x; l < NV; l += blockDim.x) {
+    const df2 c = df_from_double(y[l]);
+    const unsigned mb = qmax[(size_t)l * P + b];
+    kc[l] = make_float4(c.hi, c.lo, qgrid_scale(mb), qgrid_quantum(mb));
   }
+  __syncthreads();
   double* Ub = U + (size_t)b * Nx;
   const float* Zb = Z + (size_t)b * Nx;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
-    // all NV loads first and unconditionally (slots past nz re-read the last column and carry a zero
-    // coefficient), so they are in flight together instead of one per accumulation step
+    // all NV loads first, so they are in flight together instead of one per accumulation step
     float zv[NV];
 #pragma unroll
-    for (int l = 0; l < NV; ++l) zv[l] = Zb[(size_t)min(l, nz - 1) * ldz + s];
+    for (int l = 0; l < NV; ++l) zv[l] = Zb[(size_t)l * ldz + s];
     const double u0 = Ub[s];
     dacc a = dacc_zero();
 #pragma unroll
-    for (int l = 0; l < NV; ++l) dacc_fma(a, c[l], qgrid_value(zv[l], sc[l], qu[l]));
+    for (int l = 0; l < NV; ++l) {
+      const float4 k = kc[l];
+      dacc_fma(a, df2{k.x, k.y}, qgrid_value(zv[l], k.z, k.w));
+    }
     const df2 r = dacc_get(a);
     Ub[s] = (u0 + (double)r.hi) + (double)r.lo;
   }
@@ -590,8 +604,15 @@ int vec_update_q(sg_ctx* h, double* U, const float* Z, size_t ldz, int nz, const
     double* ydev = h->red_out + 2 * MAXOUT;
     std::copy(y_host + c0, y_host + c0 + cn, h->red_host + 2 * MAXOUT);
     SG_CUDA(h, cudaMemcpyAsync(ydev, h->red_host + 2 * MAXOUT, sizeof(double) * cn, cudaMemcpyHostToDevice, h->stream));
-    k_update_q<16><<<dim3(gx, h->P), 256, 0, h->stream>>>(U, Z + (size_t)c0 * ldz, ldz, cn, ydev, h->Nx,
-                                                          qmax + (size_t)c0 * h->P, h->P);
+    const float* Zc = Z + (size_t)c0 * ldz;
+    const unsigned* qc = qmax + (size_t)c0 * h->P;
+    switch (cn) {                                  // the exact column count: no idle slots
+#define SG_C(K) \
+      case K: k_update_q<K><<<dim3(gx, h->P), 256, 0, h->stream>>>(U, Zc, ldz, ydev, h->Nx, qc, h->P); break;
+      SG_C(1) SG_C(2) SG_C(3) SG_C(4) SG_C(5) SG_C(6) SG_C(7) SG_C(8) SG_C(9) SG_C(10) SG_C(11) SG_C(12) SG_C(13)
+      SG_C(14) SG_C(15) SG_C(16)
+#undef SG_C
+    }
     SG_CUDA(h, cudaGetLastError());
     count_launch(h);
     SG_CUDA(h, cudaStreamSynchronize(h->stream));      // the host staging slot is reused by the next chunk
