@@ -23,6 +23,7 @@
 
 #include "df64.cuh"
 #include "sg_internal.h"
+#include "update_q.cuh"
 
 namespace {
 
@@ -167,22 +168,7 @@ __global__ void k_g_update_q(double* __restrict__ U, const float* __restrict__ Z
     kc[l] = make_float4(c.hi, c.lo, qgrid_scale(mb), qgrid_quantum(mb));
   }
   __syncthreads();
-  double* Ub = U + (size_t)b * Nx;
-  const float* Zb = Z + (size_t)c0 * ldz + (size_t)b * Nx;
-  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
-    float zv[NV];
-#pragma unroll
-    for (int l = 0; l < NV; ++l) zv[l] = Zb[(size_t)min(l, nz - 1) * ldz + s];
-    const double u0 = Ub[s];
-    dacc a = dacc_zero();
-#pragma unroll
-    for (int l = 0; l < NV; ++l) {
-      const float4 k = kc[l];
-      dacc_fma(a, df2{k.x, k.y}, __fmul_rn(__fsub_rn(__fmaf_rn(zv[l], k.z, SG_QBIAS), SG_QBIAS), k.w));
-    }
-    const df2 r = dacc_get(a);
-    Ub[s] = (u0 + (double)r.hi) + (double)r.lo;
-  }
+  update_q_block<NV>(U, Z + (size_t)c0 * ldz, ldz, kc, nz, Nx, b);
 }
 
 // U += sum_{l < k} y_l z_l for z_l stored in TZ

@@ -8,6 +8,7 @@
 
 #include "df64.cuh"
 #include "sg_internal.h"
+#include "update_q.cuh"
 
 #define SG_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
   X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
@@ -528,21 +529,13 @@ int block_absmax(sg_ctx* h, const float* Z, unsigned* qmax) {
   return SG_OK;
 }
 
-// grid value of z in a block with scale s and quantum q (SG_F32Q): (fma(z, s, 1.5 2^23) - 1.5 2^23) q,
-// exact (the difference by Sterbenz, the product a power of two times an integer below 2^22)
-__device__ __forceinline__ float qgrid_value(float z, float s, float q) {
-  return __fmul_rn(__fsub_rn(__fmaf_rn(z, s, SG_QBIAS), SG_QBIAS), q);
-}
 
-// FP64 U += sum_l y_l z'_l; grid x over the nodes of a block, grid y over the blocks.  The sum over l is
-// accumulated in double-float from the exact FP32 grid values (FP32 instructions; an FP64 multiply-add per
-// term would make this pass FP64-bound on GB300) and added to U in FP64 once.
+// FP64 U += sum_l y_l z'_l over NV grid-read FP32 columns (update_q_block); grid x over the nodes of a
+// block, grid y over the blocks; the per-column constants are formed once per CTA in shared memory.
 template <int NV>
 __global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, size_t ldz,
                            const double* __restrict__ y, size_t Nx, const unsigned* __restrict__ qmax, int P) {
   const int b = blockIdx.y;
-  // per column: the coefficient y_l as double-float and the block's grid scale and quantum, formed once
-  // per CTA in shared memory (held in registers they would be re-derived, with FP64 work, per element)
   __shared__ float4 kc[NV];
   for (int l = threadIdx.x; l < NV; l += blockDim.x) {
     const df2 c = df_from_double(y[l]);
@@ -550,23 +543,7 @@ __global__ void k_update_q(double* __restrict__ U, const float* __restrict__ Z, 
     kc[l] = make_float4(c.hi, c.lo, qgrid_scale(mb), qgrid_quantum(mb));
   }
   __syncthreads();
-  double* Ub = U + (size_t)b * Nx;
-  const float* Zb = Z + (size_t)b * Nx;
-  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < Nx; s += (size_t)gridDim.x * blockDim.x) {
-    // all NV loads first, so they are in flight together instead of one per accumulation step
-    float zv[NV];
-#pragma unroll
-    for (int l = 0; l < NV; ++l) zv[l] = Zb[(size_t)l * ldz + s];
-    const double u0 = Ub[s];
-    dacc a = dacc_zero();
-#pragma unroll
-    for (int l = 0; l < NV; ++l) {
-      const float4 k = kc[l];
-      dacc_fma(a, df2{k.x, k.y}, qgrid_value(zv[l], k.z, k.w));
-    }
-    const df2 r = dacc_get(a);
-    Ub[s] = (u0 + (double)r.hi) + (double)r.lo;
-  }
+  update_q_block<NV>(U, Z, ldz, kc, NV, Nx, b);
 }
 
 // double-float U (hi at U, lo at U + lo) += sum_l y_l z'_l
