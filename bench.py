@@ -348,7 +348,8 @@ def run_ours(args, wl, rank, world):
     if args.workload == "c3" and not args.no_fp64_compare:
         for name, o2 in (("double-float Krylov basis and Gram-Schmidt (df64), bf16 levels",
                           dict(opts, arith=sg.ARITH_DF64)),
-                         ("f32 levels and z, f64 Krylov", dict(opts, pc_prec=sg.F32))):
+                         ("f32 levels and z, f64 Krylov", dict(opts, pc_prec=sg.F32)),
+                         ("IEEE FP64 outer operator as well (arith f64), bf16 levels", dict(opts, arith=sg.ARITH_F64))):
             U2 = torch.zeros_like(U)
             ms2, i2 = timed_solves(h, F, U2, o2, args.steps, stream)
             variants[name] = {"ms_per_step": round(ms2, 3), "iterations": i2.iters, "relres_true": i2.relres_true,
