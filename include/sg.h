@@ -5,7 +5,8 @@
  * Galerkin Method" (arXiv 1304.1755).  Problem (Sec. 2, Eq. model-problem):
  *   -div(a(x, xi) grad u) = f on the unit square, u = 0 on the boundary,
  *   a = abar(x) + sum_{k=1}^M sqrt(lambda_k) b_k(x) xi_k   (Eq. truncated-KLE),
- * discretised by Q1 finite elements on a uniform (n x n)-vertex grid and a
+ * discretised by Q1 finite elements on a uniform (n x n)-vertex grid (or, with
+ * elements = SG_P1, by the paper's linear triangles on the same grid, Sec. 6) and a
  * total-degree-p orthonormal polynomial chaos (Legendre or Hermite).  The
  * Galerkin matrix is A = sum_{k=0}^M G_k (x) K_k (Eq. tensor-product); it is
  * never assembled.
