@@ -199,6 +199,18 @@ def k1_method_flops(wl):
     return N * (8 * (1 + r) + r + 16)
 
 
+def gs_fp64_fmas(N, iterations, restart):
+    """FP64 multiply-adds of classical Gram-Schmidt in an (F)GMRES(restart) solve of `iterations` Arnoldi
+    steps over vectors of N elements: at step j of a cycle, j + 1 dot products and w.w (j + 2 per element),
+    then j + 1 updates and ||w||^2 (j + 2 per element)."""
+    total, left = 0, iterations
+    while left > 0:
+        k = min(left, restart)
+        total += sum(2 * (j + 2) for j in range(k))
+        left -= k
+    return N * total
+
+
 def time_apply(h, X, Y, prec, reps=50, warm=5):
     """Median CUDA-event time (ms) of one sg_apply (Y = A X), after warm-up launches."""
     import torch
@@ -401,6 +413,15 @@ def run_ours(args, wl, rank, world):
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "clocks": clocks,
         "vs_plain_fp64": vs64,
+        # the Gram-Schmidt kernels are bound by the FP64 FMA rate (2 per SM per clock on GB300), not HBM
+        "gram_schmidt_fp64": (lambda f, ms: {
+            "fma_per_step": f, "ms_per_step": round(ms, 3),
+            "achieved_tfma_s": round(f / (ms * 1e-3) / 1e12, 4),
+            "peak_tfma_s": round(2 * 152 * 2.07e9 / 1e12, 4),
+            "frac": round(f / (ms * 1e-3) / (2 * 152 * 2.07e9), 4),
+            "peak_source": "derived: 2 FP64 FMA per SM per clock x 152 SMs x 2070 MHz"})(
+            gs_fp64_fmas(N, its[-1], wl["restart"]) if arith != sg.ARITH_DF64 else 0,
+            phase_ms[2] / args.steps) if phase_ms[2] > 0 else None,
         "variants": variants or None,
     }
     # C2's comparison: sigma in {0.1, 0.3, 0.5}, block-triangular vs block-diagonal, FP64 vs FP32

@@ -31,3 +31,12 @@ def test_workload_sizes():
     assert (c2["n"] - 2) ** 2 * math.comb(c2["M"] + c2["p"], c2["p"]) == 4_551_750
     # FP64 flop count of the canonical operator at C3: 67.2 per unknown
     assert abs(bench.k1_method_flops(c3) / ((c3["n"] - 2) ** 2 * 210) - 67.2) < 1e-9
+
+
+def test_gram_schmidt_fma_count():
+    """Classical Gram-Schmidt costs 2 (j + 2) FP64 FMA per element at Arnoldi step j of a cycle; 15 steps
+    of one FGMRES(20) cycle give 270 per element, and a restart starts the count again."""
+    import bench
+    assert bench.gs_fp64_fmas(1, 15, 20) == 270
+    assert bench.gs_fp64_fmas(10, 1, 20) == 40
+    assert bench.gs_fp64_fmas(1, 5, 3) == bench.gs_fp64_fmas(1, 3, 3) + bench.gs_fp64_fmas(1, 2, 3)
