@@ -1,6 +1,7 @@
 """The paper's own discretisation on the GPU (Sec. 6: linear triangles, point Gauss-Seidel V-cycles)
 against the oracle's version of it (``oracle.p1``): the SG operator, the V-cycle in lexicographic and
-red-black order, the block preconditioners, and the five methods' iteration counts and solutions."""
+red-black order, the block preconditioners (B_S flat and recursive), and the methods' iteration counts and
+solutions."""
 import numpy as np
 import pytest
 
