@@ -173,7 +173,7 @@ int apply_precond(sg_ctx* h, int pc, int rprec, const void* R, void* Z, int prec
 // used.  The Gram-Schmidt kernels stream whole padded vectors and rely on zero padding, which
 // the other layout's vectors do not leave behind, so a change of layout clears the basis.
 int ensure_krylov(sg_ctx* h, int nv, int nz, int zprec, int layout = -1) {
-  const size_t N = h->Nx * (size_t)h->P, Np = h->Np;
+  const size_t Np = h->Np;
   if (h->kv_cap < nv) {
     cudaFree(h->kv);
     h->kv = nullptr;

@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(NT) k_axpys(const double* __restrict__ V, size
 }
 
 // ---- double-float vectors: hi[0..N), lo[N..2N) ------------------------------
-__device__ __forceinline__ df2 ldf(const float* p, size_t N, size_t i) { return {p[i], p[i + N]}; }
 __device__ __forceinline__ double dacc_to_double(dacc a) { return (double)a.s + (double)a.c; }
 
 template <int NV>
